@@ -1,0 +1,104 @@
+"""Pins of the oracle's exact-K routines against closed forms and identities.
+
+Eq. (1) (K = Tr of the pseudo-inverse of the normalised Laplacian) is computed
+by a dense eigendecomposition; it is pinned here to spectra known in closed
+form, to the single-spanning-tree case of the forest formula (Theorem 1) and
+to the grounded-Laplacian identity (corrected Eq. (3)).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2511_16356_gb300 import synth as S
+
+
+@pytest.mark.parametrize("n", [2, 3, 5, 17, 64])
+def test_complete_graph(n):
+    assert O.K_dense(S.complete(n)) == pytest.approx((n - 1) ** 2 / n, rel=1e-12)
+
+
+@pytest.mark.parametrize("n", [3, 4, 7, 30, 101])
+def test_cycle(n):
+    assert O.K_dense(S.cycle(n)) == pytest.approx((n * n - 1) / 6.0, rel=1e-11)
+
+
+@pytest.mark.parametrize("n", [3, 6, 40])
+def test_star(n):
+    assert O.K_dense(S.star(n)) == pytest.approx(n - 1.5, rel=1e-12)
+
+
+@pytest.mark.parametrize("a,b", [(1, 4), (2, 3), (5, 7)])
+def test_complete_bipartite(a, b):
+    assert O.K_dense(S.complete_bipartite(a, b)) == pytest.approx(a + b - 1.5, rel=1e-12)
+
+
+@pytest.mark.parametrize("a,b", [(3, 3), (4, 6), (7, 5)])
+def test_torus(a, b):
+    assert O.K_dense(S.torus(a, b)) == pytest.approx(O.K_torus(a, b), rel=1e-11)
+
+
+@pytest.mark.parametrize("k", [1, 3, 6])
+def test_hypercube(k):
+    assert O.K_dense(S.hypercube(k)) == pytest.approx(O.K_hypercube(k), rel=1e-11)
+
+
+def test_hypercube_closed_form_small_values():
+    # Q1 = K2: K = 1/2 ; Q2 = C4: K = (16-1)/6
+    assert O.K_hypercube(1) == pytest.approx(0.5)
+    assert O.K_hypercube(2) == pytest.approx(15 / 6)
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_tree_graphs(seed):
+    # random trees (Pruefer-like via random parent), K = (1/2m) sum_e vol_e (2m - vol_e)
+    rng = np.random.default_rng(seed)
+    n = 25
+    par = [int(rng.integers(0, v)) for v in range(1, n)]
+    g = S.csr_from_edges(n, np.arange(1, n), par)
+    assert O.K_dense(g) == pytest.approx(O.K_tree_graph(g), rel=1e-11)
+    p = S.path(9)
+    assert O.K_dense(p) == pytest.approx(O.K_tree_graph(p), rel=1e-12)
+
+
+@pytest.mark.parametrize("seed", [3, 4, 5])
+def test_grounded_formula_equals_eigen(seed):
+    g = S.random_connected(30, 0.15, seed)
+    k = O.K_dense(g)
+    for r in [0, 7, 29]:
+        assert O.K_grounded(g, r) == pytest.approx(k, rel=1e-10)
+
+
+def test_eq3_sign_erratum():
+    """Eq. (3) holds with a minus sign; as printed (plus) it gives 4 on K3 instead of 4/3."""
+    g = S.complete(3)
+    assert O.K_eq3(g, 0, -1.0) == pytest.approx(4.0 / 3.0, rel=1e-12)
+    assert O.K_eq3(g, 0, +1.0) == pytest.approx(4.0, rel=1e-12)
+    g = S.random_connected(12, 0.4, 8)
+    assert O.K_eq3(g, 3, -1.0) == pytest.approx(O.K_dense(g), rel=1e-10)
+
+
+@pytest.mark.parametrize("gname", ["K4", "grid3x3", "rc6"])
+def test_forest_formula_theorem1(gname):
+    g = {"K4": S.complete(4), "grid3x3": S.grid(3, 3), "rc6": S.random_connected(6, 0.6, 11)}[gname]
+    k = O.K_dense(g)
+    for r in range(g.n):
+        assert O.K_forest_formula(g, r) == pytest.approx(k, rel=1e-12)
+
+
+def test_kirchhoff_matches_enumeration():
+    for g in [S.complete(5), S.grid(3, 3), S.random_connected(7, 0.5, 2), S.torus(3, 3)]:
+        assert len(O.spanning_trees(g)) == round(O.kirchhoff_count(g))
+    assert len(O.spanning_trees(S.complete(5))) == 5 ** 3  # Cayley
+
+
+def test_hoeffding_sample_size_matches_theorem5_shape():
+    # omega = ceil(8 m^2 ecc^2 ln(2/delta) / (kmin^2 eps^2)) with kmin = (n-1)^2/n
+    n, m, ecc, eps, delta = 2000, 8000, 5, 0.01, 0.01
+    kmin = (n - 1) ** 2 / n
+    want = math.ceil(8 * m * m * ecc * ecc * math.log(2 / delta) / (kmin ** 2 * eps ** 2))
+    assert O.hoeffding_trees(n, m, ecc, eps, delta) == want
+    # kappa >= (n-1)^2/n holds with equality on K_n (the bound the proof needs)
+    for n in [3, 6, 11]:
+        assert O.K_dense(S.complete(n)) == pytest.approx((n - 1) ** 2 / n)
