@@ -1,0 +1,239 @@
+/*
+ * kc.h -- C ABI of the GB300 (sm_103a) implementation of the 2-forest /
+ * tree-to-forest (TTF) Kemeny-constant estimator of Li, Liao, Li and Wang,
+ * "Scalable and Provable Kemeny Constant Computation on Static and Dynamic
+ * Graphs: A 2-Forest Sampling Approach".
+ *
+ * The library samples uniform spanning trees with Wilson's loop-erased walk
+ * (Sec. 2.2; Algorithm 1 "wilson(G, r)"), traverses each tree (subtree sizes,
+ * volumes, depths, DFN: Algorithm 1 and Sec. 3.2), evaluates the per-tree
+ * path-mapping value f(tau) of Theorem 3, and averages
+ *     K_hat = sum_i w_i f(tau_i) / (2m sum_i w_i)
+ * (Theorem 3: w_i = 1; Algorithm 3 uses per-tree weights after updates).
+ * Sample maintenance after edge insertions and deletions follows Algorithm 2
+ * (BSM) and Algorithm 3 (ISM).  Every step of the path runs in CUDA kernels on
+ * one GPU; this header is plain C (no CUDA or torch types).
+ *
+ * Conventions for every call:
+ *  - Every function returns a kc_status; nothing throws or aborts across the
+ *    ABI.  On error the handle is left as it was before the call.
+ *  - Array arguments are HOST pointers owned by the caller, unless the handle
+ *    was created with kc_config.inputs_on_device = 1 (then the graph arrays of
+ *    kc_graph_create are device pointers).  The library copies what it needs;
+ *    the caller may free its arrays after the call returns.
+ *  - Vertices are 0 .. n-1.  The graph must be simple, undirected (both
+ *    directions present), connected, n >= 2 (Sec. 2.1), given in CSR with each
+ *    row sorted strictly ascending (neighbour index k means the k-th smallest
+ *    neighbour id; this fixes the random-walk stream).
+ *  - One handle must not be used by two host threads at once.  Work runs on the
+ *    handle's CUDA stream (kc_graph_set_stream); calls that return results to
+ *    the host synchronise that stream.
+ *
+ * Random-number contract (the paper only asks for a uniform neighbour):
+ * Philox4x32-10 (Salmon et al., SC'11) with key = (seed low 32, seed high 32)
+ * and counter = (vertex u, departure index k of u, sample id, tag << 24 | retry);
+ * the walk leaves u on its k-th departure along neighbour
+ * Lemire-bounded(word, deg(u)), trying the block's four words in order and
+ * bumping `retry` if all four are rejected.  Keying arrows by (u, k) makes a
+ * tree and its step count independent of the order in which walks start
+ * (Wilson's cycle-popping argument), so any launch shape gives the same trees.
+ */
+#ifndef KC_H
+#define KC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define KC_ABI_VERSION 1
+
+typedef enum {
+    KC_OK = 0,
+    KC_ERR_INVALID_ARG = 1,    /* NULL handle/pointer, n < 2, bad sizes or options  */
+    KC_ERR_NOT_SYMMETRIC = 2,  /* some (u,v) present without (v,u)                  */
+    KC_ERR_SELF_LOOP = 3,      /* some (u,u)                                         */
+    KC_ERR_MULTI_EDGE = 4,     /* a row not strictly ascending (repeat or unsorted) */
+    KC_ERR_DISCONNECTED = 5,   /* the graph (or G' after a deletion) is disconnected */
+    KC_ERR_OVERFLOW = 6,       /* 4 m^2 ecc(r) >= 2^62: int64 f(tau) could overflow  */
+    KC_ERR_OUT_OF_MEMORY = 7,  /* device allocation failed                           */
+    KC_ERR_CUDA = 8,           /* any other CUDA runtime error                       */
+    KC_ERR_STEP_LIMIT = 9,     /* a Wilson walk exceeded kc_config.step_cap          */
+    KC_ERR_EDGE_EXISTS = 10,   /* insert of an edge already present                  */
+    KC_ERR_EDGE_MISSING = 11,  /* delete of an edge not present                      */
+    KC_ERR_BRIDGE = 12,        /* delete of a bridge (G' would be disconnected)      */
+    KC_ERR_NO_SAMPLES = 13,    /* estimate/update needs at least one sampled tree    */
+    KC_ERR_NO_DEVICE = 14,     /* no CUDA device, or not an sm_103 device            */
+    KC_ERR_NOT_RETAINED = 15   /* trees were not kept (keep_trees = 0)               */
+} kc_status;
+
+/* TTF traversal variant (Theorem 8: O(n min(Delta, log n)) per tree). */
+enum { KC_TTF_AUTO = 0,   /* SCAN when ecc(r) <= 2 log2 n, else BIT           */
+       KC_TTF_SCAN = 1,   /* per-vertex walk up tau0 (O(n ecc)), all vertices in parallel */
+       KC_TTF_BIT = 2 };  /* Algorithm 1's DFS with a BIT over the tau0 DFN     */
+
+/* Stopping rule of kc_estimate. */
+enum { KC_STOP_CLT = 0,        /* z_{1-delta/2} s / sqrt(w) <= eps K_hat (1 - eps), w >= 64 */
+       KC_STOP_HOEFFDING = 1 }; /* Theorem 5 sample size (Delta read as ecc(r), kappa >= (n-1)^2/n) */
+
+/* Sample maintenance (Sec. 4). */
+enum { KC_UPDATE_BSM = 0,      /* Algorithm 2 */
+       KC_UPDATE_ISM = 1 };    /* Algorithm 3 */
+
+/* Effective resistance source for insertions (Algorithm 2/3 "Compute R(u,v)"). */
+enum { KC_R_CG = 0,            /* FP64 conjugate gradients on the Laplacian, on the device */
+       KC_R_GIVEN = 1 };       /* kc_edge_op.r supplies R(u,v) in G + (u,v)               */
+
+typedef struct {
+    uint32_t struct_size;       /* sizeof(kc_config), for ABI growth              */
+    int32_t root;               /* -1: highest degree, smallest id on ties (Exp-III) */
+    int32_t ttf_variant;        /* KC_TTF_*                                         */
+    int32_t keep_trees;         /* 1: retain parent arrays (needed by kc_update,
+                                   kc_get_tree of updated trees); 0: static mode      */
+    int32_t stop_rule;          /* KC_STOP_*                                         */
+    int32_t refresh_after_update; /* 1: recompute f of every retained tree after each
+                                   update (exactly unbiased); 0: keep stale f of
+                                   untouched trees (the paper's Theorem on BSM)     */
+    int32_t inputs_on_device;   /* 1: kc_graph_create arrays are device pointers      */
+    int32_t r_source;           /* KC_R_*                                            */
+    int64_t max_trees_in_flight; /* 0: chosen from free device memory               */
+    int64_t batch_trees;        /* kc_estimate batch size (0: 1024)                 */
+    int64_t max_trees;          /* kc_estimate cap on the pool size (0: 1 << 24)     */
+    int64_t step_cap;           /* per-tree cap on Wilson steps (0: max(2^22, 1024 n)) */
+    double mem_fraction;        /* share of free device memory for workspaces (0: 0.6) */
+} kc_config;
+
+/* Fill *cfg with the defaults listed above. */
+void kc_config_default(kc_config *cfg);
+
+typedef struct kc_graph kc_graph; /* opaque; owns device copies of everything */
+
+/*
+ * Build a handle from an undirected connected CSR graph (Sec. 2.1).
+ *  n        number of vertices (>= 2)
+ *  row_off  int64[n+1], row_off[0] = 0, row_off[n] = 2m
+ *  col      int32[2m], each row sorted strictly ascending, symmetric
+ *  cfg      NULL for defaults
+ *  out      receives the handle (NULL on error)
+ * Runs graph validation, root choice, the BFS tree tau0 (parent = smallest-id
+ * neighbour one level closer to r), its DFN and ecc(r) on the device
+ * (Algorithm 1, first three lines).
+ * Errors: INVALID_ARG, NOT_SYMMETRIC, SELF_LOOP, MULTI_EDGE, DISCONNECTED,
+ * OVERFLOW, OUT_OF_MEMORY, NO_DEVICE, CUDA.
+ */
+kc_status kc_graph_create(int64_t n, const int64_t *row_off, const int32_t *col,
+                          const kc_config *cfg, kc_graph **out);
+
+/* Release every device and host resource of the handle.  NULL is accepted. */
+kc_status kc_graph_destroy(kc_graph *g);
+
+/* Use `cuda_stream` (a cudaStream_t, NULL = legacy default) for all later work. */
+kc_status kc_graph_set_stream(kc_graph *g, void *cuda_stream);
+
+/*
+ * Draw n_trees uniform spanning trees rooted at r with sample ids
+ * [pool, pool + n_trees) under `seed` (Algorithm 1 loop: wilson, subtree
+ * volumes, DFS).  Appends each tree's f(tau) (int64, exact), step count and
+ * unit weight to the pool; with keep_trees the parent array is kept too.  The
+ * first call fixes the handle's seed; later calls must pass the same seed
+ * (KC_ERR_INVALID_ARG otherwise) so sample ids are never reused.
+ * Errors: INVALID_ARG, OUT_OF_MEMORY, STEP_LIMIT, CUDA.
+ */
+kc_status kc_sample(kc_graph *g, uint64_t seed, int64_t n_trees);
+
+/*
+ * Kemeny constant estimate K_hat = sum w f / (2m sum w) over the pool,
+ * sampling more trees first (with the handle's seed, or 0 if none was set)
+ * until the stopping rule for relative error eps at failure probability delta
+ * holds (Theorem 5; KC_STOP_CLT by default).  eps <= 0 returns the estimate of
+ * the current pool without sampling.  K_out receives K_hat.
+ * Errors: INVALID_ARG, NO_SAMPLES, OUT_OF_MEMORY, STEP_LIMIT, CUDA.
+ */
+kc_status kc_estimate(kc_graph *g, double eps, double delta, double *K_out);
+
+/* One edge update (Sec. 4): op 0 = insert (u,v) (Ins), op 1 = delete (Del). */
+typedef struct {
+    int32_t u, v;
+    int32_t op;       /* 0 insert, 1 delete */
+    int32_t pad;
+    double r;         /* R(u,v) in the graph containing (u,v); used when r_source = KC_R_GIVEN */
+} kc_edge_op;
+
+/*
+ * Apply ops in array order, each as one paper update (Algorithm 2 when
+ * mode = KC_UPDATE_BSM, Algorithm 3 when mode = KC_UPDATE_ISM), maintaining
+ * the retained trees, their f and weights.  The whole batch is validated
+ * against the evolving graph first; on any invalid op nothing is applied.
+ * Requires keep_trees.  Errors: INVALID_ARG, EDGE_EXISTS, EDGE_MISSING,
+ * BRIDGE, NO_SAMPLES, NOT_RETAINED, OUT_OF_MEMORY, STEP_LIMIT, CUDA.
+ */
+kc_status kc_update(kc_graph *g, const kc_edge_op *ops, int64_t n_ops, int32_t mode);
+
+/*
+ * Test hook: everything computed for one sample (pool index `sample`).
+ * Any output pointer may be NULL.  Arrays have n entries (host memory):
+ * parent (parent[r] = -1), depth, DFN in/out (preorder from 0, children in
+ * ascending id, out = in + size - 1), vol (subtree volume, int64).  Scalars:
+ * f (int64), steps (Wilson departures).  For trees never updated the arrays are
+ * recomputed on the device from (seed, sample id); updated trees need
+ * keep_trees.  Errors: INVALID_ARG, NOT_RETAINED, OUT_OF_MEMORY, CUDA.
+ */
+kc_status kc_get_tree(kc_graph *g, int64_t sample, int32_t *parent, int32_t *depth,
+                      int32_t *dfn_in, int32_t *dfn_out, int64_t *vol, int64_t *f,
+                      int64_t *steps);
+
+/*
+ * Copy the pool's per-tree values to host arrays of length count starting at
+ * pool index first (any pointer may be NULL): f (int64), weight (fp64),
+ * steps (int64), sample id (int64).  Errors: INVALID_ARG, CUDA.
+ */
+kc_status kc_get_samples(kc_graph *g, int64_t first, int64_t count, int64_t *f, double *weight,
+                         int64_t *steps, int64_t *sample_id);
+
+/*
+ * The fixed tree tau0 (host arrays of n entries, any may be NULL): parent p0
+ * (p0[r] = -1), BFS level, DFN in0/out0; scalars root and ecc(r).
+ */
+kc_status kc_get_tau0(kc_graph *g, int32_t *p0, int32_t *level, int32_t *in0, int32_t *out0,
+                      int32_t *root, int32_t *ecc);
+
+typedef struct {
+    int64_t n, m;
+    int32_t root, ecc;
+    int32_t ttf_variant;         /* resolved KC_TTF_SCAN or KC_TTF_BIT */
+    int32_t pad;
+    int64_t pool_trees;          /* trees in the pool                        */
+    int64_t next_sample_id;      /* never-reused sample id counter           */
+    int64_t total_steps;         /* sum of Wilson departures over all samples */
+    int64_t trees_in_flight;     /* wave size used by the last kc_sample      */
+    int64_t pool_bytes;          /* device bytes held by the pool            */
+    int64_t workspace_bytes;     /* device bytes held by wave workspaces     */
+    int64_t updates_applied;
+    int64_t trees_resampled;     /* trees replaced or transformed by updates  */
+    /* device time (ms, CUDA events on the handle's stream) and launches, per phase */
+    double ms_wilson, ms_traverse, ms_ttf, ms_reduce, ms_update, ms_setup;
+    int64_t launches_wilson, launches_traverse, launches_ttf, launches_reduce,
+            launches_update, launches_setup;
+    /* sums over the pool: exact sum of w=1 f as two int64 limbs, and FP64 moments */
+    int64_t f_sum_hi;            /* high limb (signed) of the int128 sum of f */
+    uint64_t f_sum_lo;           /* low limb of the int128 sum of f           */
+    double wf_sum, w_sum, x2_sum; /* sum w f/(2m), sum w, sum (f/2m)^2 over the pool */
+} kc_stats_t;
+
+kc_status kc_stats(kc_graph *g, kc_stats_t *out);
+
+/* Zero the per-phase timers and launch counters of kc_stats. */
+kc_status kc_reset_timers(kc_graph *g);
+
+/* Static description of a status code (never NULL). */
+const char *kc_status_string(kc_status s);
+
+/* Last CUDA error text seen by this handle (empty if none). */
+const char *kc_last_error(kc_graph *g);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* KC_H */

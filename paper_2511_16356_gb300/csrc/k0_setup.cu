@@ -1,0 +1,197 @@
+// Graph setup on the device: CSR validation, walk records, root choice, the
+// BFS tree tau0 (Algorithm 1, "Generate tau0 using BFS with root r") and a
+// parent-first order of tau0 for the traversal passes.
+#include "kc_common.cuh"
+
+namespace kc {
+
+namespace {
+
+__global__ void k_build_records(GraphView g, VRec *rec, int32_t *deg) {
+    const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= g.n) return;
+    const int64_t off = g.row_off[v];
+    const int32_t d = (int32_t)(g.row_off[v + 1] - off);
+    VRec r;
+    r.deg = d;
+    r.off_lo = (uint32_t)off;
+    r.off_hi = (uint32_t)((uint64_t)off >> 32);
+#pragma unroll
+    for (int k = 0; k < kInline; ++k) r.nbr[k] = k < d ? g.col[off + k] : -1;
+    rec[v] = r;
+    deg[v] = d;
+}
+
+// flags: 1 column out of range, 2 self loop, 4 row not strictly ascending,
+//        8 missing reverse edge, 16 isolated vertex
+__global__ void k_validate(GraphView g, uint32_t *flags) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t n = g.n;
+    if (e < n && g.row_off[e + 1] == g.row_off[e]) atomicOr(flags, 16u);
+    if (e >= g.twom) return;
+    // source row of entry e: largest v with row_off[v] <= e
+    int64_t lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int64_t mid = (lo + hi + 1) >> 1;
+        if (g.row_off[mid] <= e) lo = mid; else hi = mid - 1;
+    }
+    const int64_t v = lo;
+    const int32_t w = g.col[e];
+    uint32_t f = 0;
+    if (w < 0 || w >= n) { atomicOr(flags, 1u); return; }
+    if (w == v) f |= 2u;
+    if (e + 1 < g.row_off[v + 1] && g.col[e + 1] <= w) f |= 4u;
+    // reverse edge (w, v) by binary search in row w
+    int64_t a = g.row_off[w], b = g.row_off[w + 1] - 1;
+    bool found = false;
+    while (a <= b) {
+        const int64_t mid = (a + b) >> 1;
+        const int32_t c = g.col[mid];
+        if (c == v) { found = true; break; }
+        if (c < v) a = mid + 1; else b = mid - 1;
+    }
+    if (!found) f |= 8u;
+    if (f) atomicOr(flags, f);
+}
+
+// Highest degree, smallest id on ties: maximise (deg << 32) | (2^32 - 1 - v).
+__global__ void k_root(GraphView g, unsigned long long *best) {
+    const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= g.n) return;
+    const unsigned long long key =
+        ((unsigned long long)(uint32_t)g.deg[v] << 32) | (0xFFFFFFFFull - (unsigned long long)v);
+    atomicMax(best, key);
+}
+
+__global__ void k_bfs_init(int64_t n, int32_t r, int32_t *level) {
+    const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v < n) level[v] = (v == r) ? 0 : -1;
+}
+
+// One level-synchronous BFS round: every vertex on level `lev` labels its
+// unlabelled neighbours lev + 1 (all writers store the same value).
+__global__ void k_bfs_level(GraphView g, int32_t lev, int32_t *level, int32_t *changed) {
+    const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= g.n || level[v] != lev) return;
+    bool any = false;
+    for (int64_t e = g.row_off[v]; e < g.row_off[v + 1]; ++e) {
+        const int32_t w = g.col[e];
+        if (level[w] < 0) { level[w] = lev + 1; any = true; }
+    }
+    if (any) *changed = 1;
+}
+
+// tau0 parent: the smallest-id neighbour one level closer to r (rows ascend).
+__global__ void k_bfs_parent(GraphView g, const int32_t *level, int32_t *p0, int32_t *unreached) {
+    const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= g.n) return;
+    const int32_t lv = level[v];
+    if (lv < 0) { atomicAdd(unreached, 1); p0[v] = -1; return; }
+    int32_t p = -1;
+    if (lv > 0) {
+        for (int64_t e = g.row_off[v]; e < g.row_off[v + 1]; ++e) {
+            const int32_t w = g.col[e];
+            if (level[w] == lv - 1) { p = w; break; }
+        }
+    }
+    p0[v] = p;
+}
+
+__global__ void k_tau0_words(int64_t n, const int32_t *p0, const int32_t *level, uint64_t *word) {
+    const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v < n) word[v] = w_make(p0[v], (uint32_t)level[v], true);
+}
+
+__global__ void k_level_hist(int64_t n, const int32_t *level, int32_t *hist) {
+    const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v < n) atomicAdd(hist + level[v], 1);
+}
+
+// exclusive scan of hist[0..L] in place by one block (L is the eccentricity + 1)
+__global__ void k_scan_small(int32_t *hist, int32_t L) {
+    __shared__ int32_t carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int32_t base = 0; base < L; base += blockDim.x) {
+        const int32_t i = base + threadIdx.x;
+        int32_t x = i < L ? hist[i] : 0;
+        // block inclusive scan (Hillis-Steele in shared memory)
+        __shared__ int32_t buf[1024];
+        buf[threadIdx.x] = x;
+        __syncthreads();
+        for (int d = 1; d < (int)blockDim.x; d <<= 1) {
+            const int32_t y = threadIdx.x >= (unsigned)d ? buf[threadIdx.x - d] : 0;
+            __syncthreads();
+            buf[threadIdx.x] += y;
+            __syncthreads();
+        }
+        const int32_t incl = buf[threadIdx.x];
+        const int32_t c = carry;
+        if (i < L) hist[i] = c + incl - x;
+        __syncthreads();
+        if (threadIdx.x == blockDim.x - 1) carry = c + incl;
+        __syncthreads();
+    }
+}
+
+__global__ void k_level_scatter(int64_t n, const int32_t *level, int32_t *offs, int32_t *ord) {
+    const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v < n) ord[atomicAdd(offs + level[v], 1)] = (int32_t)v;
+}
+
+inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+}  // namespace
+
+cudaError_t launch_build_records(const GraphView &g, VRec *rec, int32_t *deg, cudaStream_t s) {
+    k_build_records<<<blocks_for(g.n, 256), 256, 0, s>>>(g, rec, deg);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_validate(const GraphView &g, uint32_t *flags, cudaStream_t s) {
+    const int64_t work = g.twom > g.n ? g.twom : g.n;
+    k_validate<<<blocks_for(work, 256), 256, 0, s>>>(g, flags);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_root(const GraphView &g, unsigned long long *best, cudaStream_t s) {
+    k_root<<<blocks_for(g.n, 256), 256, 0, s>>>(g, best);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bfs_init(int64_t n, int32_t r, int32_t *level, cudaStream_t s) {
+    k_bfs_init<<<blocks_for(n, 256), 256, 0, s>>>(n, r, level);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bfs_level(const GraphView &g, int32_t lev, int32_t *level, int32_t *changed,
+                             cudaStream_t s) {
+    k_bfs_level<<<blocks_for(g.n, 256), 256, 0, s>>>(g, lev, level, changed);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bfs_parent(const GraphView &g, const int32_t *level, int32_t *p0,
+                              int32_t *unreached, cudaStream_t s) {
+    k_bfs_parent<<<blocks_for(g.n, 256), 256, 0, s>>>(g, level, p0, unreached);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tau0_words(int64_t n, const int32_t *p0, const int32_t *level, uint64_t *word,
+                              cudaStream_t s) {
+    k_tau0_words<<<blocks_for(n, 256), 256, 0, s>>>(n, p0, level, word);
+    return cudaGetLastError();
+}
+
+// Parent-first order of tau0: vertices sorted by BFS level (order inside a
+// level is irrelevant to the traversal passes).  hist needs ecc + 1 entries.
+cudaError_t launch_level_order(int64_t n, int32_t ecc, const int32_t *level, int32_t *hist,
+                               int32_t *ord, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(hist, 0, sizeof(int32_t) * (size_t)(ecc + 1), s);
+    if (e != cudaSuccess) return e;
+    k_level_hist<<<blocks_for(n, 256), 256, 0, s>>>(n, level, hist);
+    k_scan_small<<<1, 1024, 0, s>>>(hist, ecc + 1);
+    k_level_scatter<<<blocks_for(n, 256), 256, 0, s>>>(n, level, hist, ord);
+    return cudaGetLastError();
+}
+
+}  // namespace kc

@@ -1,0 +1,176 @@
+// Per-tree traversal passes (Algorithm 1, "vol[u] <- the volume of Sub(tau_i, u)";
+// DFN of Sec. 3.2 "Implementation Details").
+//
+// A warp owns one tree and walks its vertices 32 at a time, so every pass costs
+// one or two dependent gathers per 32 vertices instead of one per vertex.
+// Dependencies inside a chunk are resolved with warp shuffles:
+//   (a) bottom-up, over the parent-first order in reverse: size and volume
+//       (vol = sum of degrees over the subtree).  A child inside the chunk hands
+//       its total to its parent lane; a parent outside the chunk receives an
+//       integer atomic add (order-independent, so results are exact).
+//   (b) sibling offsets, over vertex ids ascending: among the children of one
+//       parent (grouped with __match_any_sync) the offset of child c is the sum
+//       of the sizes of its smaller-id siblings; a per-parent running sum
+//       carries it across chunks.
+//   (c) top-down, over the parent-first order: in[v] = in[p] + 1 + offset(v),
+//       chains inside the chunk resolved by pointer jumping (5 rounds).
+// The resulting DFN is the preorder from 0 that visits children in ascending id;
+// out[v] = in[v] + size[v] - 1.
+#include "kc_common.cuh"
+
+namespace kc {
+
+namespace {
+
+constexpr unsigned kFull = 0xFFFFFFFFu;
+
+__device__ __forceinline__ int32_t ld_cg(const int32_t *p) { return __ldcg(p); }
+__device__ __forceinline__ int64_t ld_cg(const int64_t *p) {
+    return (int64_t)__ldcg((const long long *)p);
+}
+
+__global__ void __launch_bounds__(128) k_bottom_up(GraphView g, WaveView w) {
+    const int lane = threadIdx.x & 31;
+    const int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (t >= w.B) return;
+    const int64_t n = g.n;
+    const int32_t *__restrict__ ord = w.ord + t * n;
+    const uint64_t *__restrict__ word = w.word + t * n;
+    int32_t *size = w.size + t * n;
+    int64_t *vol = w.vol + t * n;
+    for (int64_t base = n - 1; base >= 0; base -= 32) {
+        const int64_t p = base - lane;
+        const bool act = p >= 0;
+        int32_t v = -1, par = -2, s_own = 0;
+        int64_t v_own = 0;
+        if (act) {
+            v = ord[p];
+            par = w_next(word[v]);
+            s_own = 1 + ld_cg(size + v);
+            v_own = (int64_t)g.deg[v] + ld_cg(vol + v);
+        }
+        // lane 0 holds the latest vertex in the order; a parent always sits at a
+        // higher lane than its children in the same chunk.
+        bool parent_here = false;
+#pragma unroll 4
+        for (int j = 0; j < 32; ++j) {
+            const int32_t vj = __shfl_sync(kFull, v, j);
+            const int32_t pj = __shfl_sync(kFull, par, j);
+            const int32_t sj = __shfl_sync(kFull, s_own, j);
+            const int64_t volj = __shfl_sync(kFull, v_own, j);
+            if (act && j < lane && pj == v) { s_own += sj; v_own += volj; }
+            if (act && j > lane && vj == par) parent_here = true;
+        }
+        if (act) {
+            __stcg(size + v, s_own);
+            __stcg((long long *)(vol + v), (long long)v_own);
+            if (par >= 0 && !parent_here) {
+                atomicAdd(size + par, s_own);
+                atomicAdd((unsigned long long *)(vol + par), (unsigned long long)v_own);
+            }
+        }
+        __threadfence_block();
+        __syncwarp();
+    }
+}
+
+__global__ void __launch_bounds__(128) k_sibling_offsets(GraphView g, WaveView w) {
+    const int lane = threadIdx.x & 31;
+    const int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (t >= w.B) return;
+    const int64_t n = g.n;
+    const uint64_t *__restrict__ word = w.word + t * n;
+    const int32_t *__restrict__ size = w.size + t * n;
+    int32_t *din = w.din + t * n;
+    int32_t *run = w.aux + t * n;  // per-parent running sum of sizes, zeroed
+    for (int64_t base = 0; base < n; base += 32) {
+        const int64_t v = base + lane;
+        const bool act = v < n;
+        const int32_t par = act ? w_next(word[v]) : -2;
+        const int32_t sz = act ? size[v] : 0;
+        const unsigned grp = __match_any_sync(kFull, par);
+        int32_t excl = 0, tot = 0;
+#pragma unroll 8
+        for (int j = 0; j < 32; ++j) {
+            const int32_t sj = __shfl_sync(kFull, sz, j);
+            const bool same = (grp >> j) & 1u;
+            if (same) {
+                tot += sj;
+                if (j < lane) excl += sj;
+            }
+        }
+        const int leader = __ffs(grp) - 1;
+        int32_t basev = 0;
+        if (lane == leader && par >= 0) basev = atomicAdd(run + par, tot);
+        basev = __shfl_sync(kFull, basev, leader);
+        if (act) din[v] = par >= 0 ? basev + excl : 0;
+        __syncwarp();
+    }
+}
+
+__global__ void __launch_bounds__(128) k_top_down(GraphView g, WaveView w, int want_pre) {
+    const int lane = threadIdx.x & 31;
+    const int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (t >= w.B) return;
+    const int64_t n = g.n;
+    const int32_t *__restrict__ ord = w.ord + t * n;
+    const uint64_t *__restrict__ word = w.word + t * n;
+    int32_t *din = w.din + t * n;
+    int32_t *pre = w.aux + t * n;
+    for (int64_t base = 0; base < n; base += 32) {
+        const int64_t p = base + lane;
+        const bool act = p < n;
+        int32_t v = -1, par = -1, off = 0;
+        if (act) {
+            v = ord[p];
+            par = w_next(word[v]);
+            off = ld_cg(din + v);
+        }
+        int ptr = -1;
+#pragma unroll 8
+        for (int j = 0; j < 32; ++j) {
+            const int32_t vj = __shfl_sync(kFull, v, j);
+            if (act && j < lane && vj == par) ptr = j;
+        }
+        int32_t val = 0;
+        if (act && par >= 0) {
+            val = 1 + off;
+            if (ptr < 0) val += ld_cg(din + par);
+        }
+#pragma unroll
+        for (int it = 0; it < 5; ++it) {
+            const int src = ptr < 0 ? lane : ptr;
+            const int32_t pv = __shfl_sync(kFull, val, src);
+            const int pp = __shfl_sync(kFull, ptr, src);
+            if (ptr >= 0) {
+                val += pv;
+                ptr = pp;
+            }
+        }
+        if (act) {
+            __stcg(din + v, val);
+            if (want_pre && val >= 0 && val < n) pre[val] = v;
+        }
+        __threadfence_block();
+        __syncwarp();
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_traverse(const GraphView &g, WaveView w, bool want_preorder, cudaStream_t s,
+                            int *launches) {
+    const size_t per = (size_t)(w.B * g.n);
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(w.size, 0, sizeof(int32_t) * per, s)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(w.vol, 0, sizeof(int64_t) * per, s)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(w.aux, 0, sizeof(int32_t) * per, s)) != cudaSuccess) return e;
+    const unsigned blocks = (unsigned)((w.B * 32 + 127) / 128);
+    k_bottom_up<<<blocks, 128, 0, s>>>(g, w);
+    k_sibling_offsets<<<blocks, 128, 0, s>>>(g, w);
+    k_top_down<<<blocks, 128, 0, s>>>(g, w, want_preorder ? 1 : 0);
+    if (launches) *launches += 3;
+    return cudaGetLastError();
+}
+
+}  // namespace kc

@@ -1,0 +1,228 @@
+// f(tau) of Theorem 3 for every tree of a wave (Sec. 3.2).
+//
+// With p(x) the tau parent, p0(x) the tau0 parent and vol(x) = vol(Sub(tau, x)),
+//   f(tau) = sum_{v != r} d(v) Q(v),
+//   Q(v)   = sum over tau-ancestors x of v (x != r, x included when x = v) of
+//              [p(x) = p0(x)]  [v in Sub(tau0, x)]    (2m - vol(x))      (forward)
+//            - [p0(p(x)) = x]  [v in Sub(tau0, p(x))] (2m - vol(x))      (reverse)
+// (Theorem 4 with the d(u) weight of Algorithm 1 and the reverse undo written as
+// the negation of its add).  Two kernels evaluate it:
+//
+//  SCAN: for each v, walk up tau0 (at most ecc(r) steps) and test tau-ancestry
+//        with the DFN intervals of tau: O(n ecc) work, all vertices of all trees
+//        in parallel.  Used when ecc(r) is small (the O(n Delta) bound of Thm 8).
+//  BIT:  Algorithm 1: a DFS over tau in preorder keeps, for the tau-ancestors of
+//        the current vertex, range adds over tau0-DFN intervals in a Fenwick
+//        array and queries the point in0(v).  O(n log n) per tree.  A warp owns a
+//        tree and handles 32 preorder positions per round: all 32 point queries
+//        are loaded first, then the 32 visits are replayed in lane order with the
+//        stack held in registers, each range add both issued to the Fenwick array
+//        (integer atomics) and folded into the pending queries of later lanes.
+#include "kc_common.cuh"
+
+namespace kc {
+
+namespace {
+
+constexpr unsigned kFull = 0xFFFFFFFFu;
+
+__global__ void __launch_bounds__(256) k_ttf_scan(GraphView g, WaveView w) {
+    const int64_t t = blockIdx.y;
+    const int64_t n = g.n;
+    const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const uint64_t *__restrict__ word = w.word + t * n;
+    const int32_t *__restrict__ din = w.din + t * n;
+    const int32_t *__restrict__ size = w.size + t * n;
+    const int64_t *__restrict__ vol = w.vol + t * n;
+    const int32_t r = g.root;
+    const int64_t twom = g.twom;
+    long long contrib = 0;
+    if (v < n && v != r) {
+        const int32_t inv = din[v];
+        long long q = 0;
+        int32_t x = (int32_t)v;
+        for (int it = 0; x != r && it <= g.ecc; ++it) {
+            const int32_t p0x = g.p0[x];
+            const int32_t px = w_next(word[x]);
+            if (px == p0x) {
+                const int32_t inx = din[x];
+                if (inx <= inv && inv <= inx + size[x] - 1) q += twom - vol[x];
+            } else if (p0x != r && w_next(word[p0x]) == x) {
+                const int32_t inw = din[p0x];
+                if (inw <= inv && inv <= inw + size[p0x] - 1) q -= twom - vol[p0x];
+            }
+            x = p0x;
+        }
+        contrib = (long long)g.deg[v] * q;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) contrib += __shfl_down_sync(kFull, contrib, o);
+    __shared__ long long part[8];
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = contrib;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        long long s = 0;
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) s += part[k];
+        if (s != 0) atomicAdd((unsigned long long *)(w.f + t), (unsigned long long)s);
+    }
+}
+
+// index of the c-th node of the Fenwick update chain starting at i (1-based)
+__device__ __forceinline__ int64_t up_chain(int64_t i, int c) {
+    for (int k = 0; k < c; ++k) i += i & (-i);
+    return i;
+}
+
+// range add [l, r] (0-based positions) += val, as two point updates
+__device__ __forceinline__ void bit_range_add(int64_t *bit, int64_t n, int lane, int32_t l,
+                                              int32_t r, long long val) {
+    // the chain strictly increases, so lane c owns its c-th node exclusively
+    const int64_t a = up_chain((int64_t)l + 1, lane);
+    if (a <= n) atomicAdd((unsigned long long *)(bit + a), (unsigned long long)val);
+    if ((int64_t)r + 2 <= n) {
+        const int64_t b = up_chain((int64_t)r + 2, lane);
+        if (b <= n) atomicAdd((unsigned long long *)(bit + b), (unsigned long long)(-val));
+    }
+}
+
+__global__ void __launch_bounds__(128) k_ttf_bit(GraphView g, WaveView w) {
+    const int lane = threadIdx.x & 31;
+    const int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (t >= w.B) return;
+    const int64_t n = g.n;
+    const int32_t r = g.root;
+    const int32_t twom = (int32_t)g.twom;  // host guarantees 2m < 2^31 for this kernel
+    const uint64_t *__restrict__ word = w.word + t * n;
+    const int32_t *__restrict__ size = w.size + t * n;
+    const int64_t *__restrict__ vol = w.vol + t * n;
+    const int32_t *__restrict__ pre = w.aux + t * n;
+    int64_t *bit = w.bit + t * (n + 1);  // zeroed, 1-based
+    int4 *stk = reinterpret_cast<int4 *>(w.stack) + t * w.stack_cap;
+    const unsigned lt_mask = (1u << lane) - 1u;
+
+    int64_t sp = 0;         // entries in the memory stack
+    long long facc = 0;     // this lane's share of f
+    for (int64_t base = 0; base < n; base += 32) {
+        const int64_t i = base + lane;
+        const bool act = i < n;
+        // ---- per-vertex data for preorder position i
+        int32_t v = -1, kind = 0, el = 0, er = 0, eval = 0, eout = 0, qpos = 0, dv = 0;
+        if (act) {
+            v = pre[i];
+            if (v < 0 || v >= n) {  // preorder is a permutation; anything else is corrupt
+                atomicOr(w.err, kErrBadTree);
+                v = r;
+            }
+            const int32_t par = w_next(word[v]);
+            qpos = g.in0[v];
+            dv = g.deg[v];
+            eout = (int32_t)i + size[v] - 1;
+            if (v != r) {
+                const int32_t vv = (int32_t)vol[v];
+                if (g.p0[v] == par) {
+                    kind = 1; el = qpos; er = g.out0[v]; eval = twom - vv;
+                } else if (par != r && g.p0[par] == v) {
+                    kind = 2; el = g.in0[par]; er = g.out0[par]; eval = vv - twom;
+                }
+            }
+        }
+        // ---- prefix sums at the start of the chunk
+        long long pf = 0;
+        if (act) {
+            for (int64_t k = (int64_t)qpos + 1; k > 0; k &= k - 1)
+                pf += __ldcg((const long long *)(bit + k));
+        }
+        // every query load must have returned before this chunk issues its own
+        // atomics: reading pf in a shuffle makes the warp wait for them
+        pf = __shfl_sync(kFull, pf, lane);
+        long long corr = 0;
+        // ---- top of the memory stack, one entry per lane (lane k: entry sp-1-k)
+        int64_t mbase = sp;   // window covers entries [mbase - 32, mbase)
+        int4 win = make_int4(0, 0, 0, 0);
+        if (mbase - 1 - lane >= 0) win = stk[mbase - 1 - lane];
+        int mtop = 0;         // entries of the window already popped
+        int64_t mpopped = 0;  // memory entries popped in this chunk
+        unsigned cmask = 0;   // chunk entries alive on the stack (push order = lane order)
+        __syncwarp();
+        for (int j = 0; j < 32; ++j) {
+            const int64_t ij = base + j;
+            if (ij >= n) break;
+            // pop every stacked ancestor whose subtree ended before position ij
+            while (true) {
+                int32_t pl, pr, pv;
+                if (cmask) {
+                    const int h = 31 - __clz(cmask);
+                    const int32_t o = __shfl_sync(kFull, eout, h);
+                    if (o >= ij) break;
+                    pl = __shfl_sync(kFull, el, h);
+                    pr = __shfl_sync(kFull, er, h);
+                    pv = __shfl_sync(kFull, eval, h);
+                    cmask &= ~(1u << h);
+                } else {
+                    if (sp - mpopped <= 0) break;
+                    if (mtop == 32) {  // reload the window below what was consumed
+                        mbase = sp - mpopped;
+                        win = make_int4(0, 0, 0, 0);
+                        if (mbase - 1 - lane >= 0) win = stk[mbase - 1 - lane];
+                        mtop = 0;
+                    }
+                    const int32_t o = __shfl_sync(kFull, win.x, mtop);
+                    if (o >= ij) break;
+                    pl = __shfl_sync(kFull, win.y, mtop);
+                    pr = __shfl_sync(kFull, win.z, mtop);
+                    pv = __shfl_sync(kFull, win.w, mtop);
+                    ++mtop;
+                    ++mpopped;
+                }
+                // undo: add the negation
+                bit_range_add(bit, n, lane, pl, pr, -(long long)pv);
+                if (lane >= j && pl <= qpos && qpos <= pr) corr -= pv;
+            }
+            const int kj = __shfl_sync(kFull, kind, j);
+            if (kj) {
+                const int32_t l = __shfl_sync(kFull, el, j);
+                const int32_t rr = __shfl_sync(kFull, er, j);
+                const int32_t val = __shfl_sync(kFull, eval, j);
+                bit_range_add(bit, n, lane, l, rr, (long long)val);
+                if (lane >= j && l <= qpos && qpos <= rr) corr += val;
+                cmask |= 1u << j;
+            }
+        }
+        if (act) facc += (long long)dv * (pf + corr);
+        // ---- spill the surviving chunk entries on top of the memory stack
+        const int64_t nsp = sp - mpopped;
+        if ((cmask >> lane) & 1u) {
+            const int64_t slot = nsp + __popc(cmask & lt_mask);
+            if (slot < w.stack_cap) stk[slot] = make_int4(eout, el, er, eval);
+        }
+        sp = nsp + __popc(cmask);
+        if (sp > w.stack_cap) {
+            if (lane == 0) atomicOr(w.err, kErrBadTree);
+            return;
+        }
+        __threadfence_block();
+        __syncwarp();
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) facc += __shfl_down_sync(kFull, facc, o);
+    if (lane == 0) w.f[t] = facc;
+}
+
+}  // namespace
+
+cudaError_t launch_ttf_scan(const GraphView &g, WaveView w, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(w.f, 0, sizeof(int64_t) * (size_t)w.B, s);
+    if (e != cudaSuccess) return e;
+    dim3 grid((unsigned)((g.n + 255) / 256), (unsigned)w.B);
+    k_ttf_scan<<<grid, 256, 0, s>>>(g, w);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ttf_bit(const GraphView &g, WaveView w, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(w.bit, 0, sizeof(int64_t) * (size_t)(w.B * (g.n + 1)), s);
+    if (e != cudaSuccess) return e;
+    k_ttf_bit<<<(unsigned)((w.B * 32 + 127) / 128), 128, 0, s>>>(g, w);
+    return cudaGetLastError();
+}
+
+}  // namespace kc

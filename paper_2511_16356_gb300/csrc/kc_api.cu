@@ -1,0 +1,800 @@
+// Host side of the C ABI declared in include/kc.h: handle lifetime, graph
+// setup, wave planning for kc_sample, the stopping rule of kc_estimate, pool
+// bookkeeping and the test hooks.  All arithmetic of the method runs in the
+// kernels of the other translation units; this file only moves data, sizes
+// launches and reads back scalars.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "kc_common.cuh"
+
+namespace kc {
+cudaError_t launch_out_from_size(int64_t n, const int32_t *din, const int32_t *size,
+                                 int32_t *dout, cudaStream_t s);
+cudaError_t launch_iota(int64_t *dst, int64_t start, int64_t count, cudaStream_t s);
+}  // namespace kc
+
+using namespace kc;
+
+namespace {
+
+struct Fail {
+    kc_status st;
+};
+
+kc_status cuda_status(cudaError_t e) {
+    return e == cudaErrorMemoryAllocation ? KC_ERR_OUT_OF_MEMORY : KC_ERR_CUDA;
+}
+
+#define KC_CK(g, expr)                                                       \
+    do {                                                                     \
+        cudaError_t _e = (expr);                                             \
+        if (_e != cudaSuccess) {                                             \
+            if (g) (g)->last_error = std::string(#expr) + ": " + cudaGetErrorString(_e); \
+            (void)cudaGetLastError();                                        \
+            throw Fail{cuda_status(_e)};                                     \
+        }                                                                    \
+    } while (0)
+
+template <class T>
+void dalloc(kc_graph *g, T **p, size_t count) {
+    *p = nullptr;
+    if (count == 0) count = 1;
+    KC_CK(g, cudaMalloc((void **)p, sizeof(T) * count));
+}
+
+template <class T>
+void dfree(T *&p) {
+    if (p) cudaFree((void *)p);
+    p = nullptr;
+}
+
+GraphView view_of(const kc_graph *g) {
+    GraphView v;
+    v.n = g->n;
+    v.twom = 2 * g->m;
+    v.row_off = g->d_row_off;
+    v.col = g->d_col;
+    v.deg = g->d_deg;
+    v.rec = g->d_rec;
+    v.root = g->root;
+    v.ecc = g->ecc;
+    v.p0 = g->d_p0;
+    v.in0 = g->d_in0;
+    v.out0 = g->d_out0;
+    return v;
+}
+
+// Phase timing with CUDA events on the handle's stream.
+struct Phase {
+    kc_graph *g;
+    PhaseTimer &t;
+    Phase(kc_graph *g_, PhaseTimer &t_) : g(g_), t(t_) { KC_CK(g, cudaEventRecord(g->ev0, g->stream)); }
+    void done(int launches) {
+        KC_CK(g, cudaEventRecord(g->ev1, g->stream));
+        KC_CK(g, cudaEventSynchronize(g->ev1));
+        float ms = 0.f;
+        KC_CK(g, cudaEventElapsedTime(&ms, g->ev0, g->ev1));
+        t.ms += ms;
+        t.launches += launches;
+    }
+};
+
+// Workspace carving ----------------------------------------------------------
+struct Plan {
+    int64_t BW = 0;        // trees per Wilson wave
+    int64_t BT = 0;        // trees per traversal sub-wave
+    bool bit = false;
+    int64_t stack_cap = 0; // BIT stack entries per tree
+};
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+size_t ws_size(const kc_graph *g, const Plan &p) {
+    const size_t n = (size_t)g->n;
+    size_t b = 0;
+    b += align256(sizeof(uint64_t) * n * p.BW);      // word
+    b += align256(sizeof(int32_t) * n * p.BW);       // ord
+    b += 3 * align256(sizeof(int64_t) * p.BW);       // steps, f, sids
+    b += align256(sizeof(int32_t) * n * p.BT);       // size
+    b += align256(sizeof(int64_t) * n * p.BT);       // vol
+    b += align256(sizeof(int32_t) * n * p.BT);       // din
+    b += align256(sizeof(int32_t) * n * p.BT);       // aux
+    if (p.bit) {
+        b += align256(sizeof(int64_t) * (n + 1) * p.BT);       // bit
+        b += align256(sizeof(int32_t) * 4 * (size_t)p.stack_cap * p.BT);  // stack
+    }
+    return b;
+}
+
+struct Carved {
+    WaveView wv;       // Wilson-wave view (B = BW), traversal fields point at sub-wave buffers
+    int64_t *sids;
+};
+
+Carved carve(kc_graph *g, const Plan &p) {
+    const size_t n = (size_t)g->n;
+    char *base = (char *)g->d_ws;
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        char *q = base + off;
+        off += align256(bytes);
+        return (void *)q;
+    };
+    Carved c;
+    WaveView &w = c.wv;
+    w.n = g->n;
+    w.B = p.BW;
+    w.word = (uint64_t *)take(sizeof(uint64_t) * n * p.BW);
+    w.ord = (int32_t *)take(sizeof(int32_t) * n * p.BW);
+    w.steps = (int64_t *)take(sizeof(int64_t) * p.BW);
+    w.f = (int64_t *)take(sizeof(int64_t) * p.BW);
+    c.sids = (int64_t *)take(sizeof(int64_t) * p.BW);
+    w.size = (int32_t *)take(sizeof(int32_t) * n * p.BT);
+    w.vol = (int64_t *)take(sizeof(int64_t) * n * p.BT);
+    w.din = (int32_t *)take(sizeof(int32_t) * n * p.BT);
+    w.aux = (int32_t *)take(sizeof(int32_t) * n * p.BT);
+    w.bit = nullptr;
+    w.stack = nullptr;
+    w.stack_cap = p.stack_cap;
+    if (p.bit) {
+        w.bit = (int64_t *)take(sizeof(int64_t) * (n + 1) * p.BT);
+        w.stack = (int32_t *)take(sizeof(int32_t) * 4 * (size_t)p.stack_cap * p.BT);
+    }
+    w.err = g->d_err;
+    w.maxdepth = (int32_t *)(g->d_err + 1);
+    return c;
+}
+
+void ensure_ws(kc_graph *g, const Plan &p) {
+    const size_t need = ws_size(g, p);
+    if (need <= g->ws_bytes) return;
+    dfree(g->d_ws);
+    g->ws_bytes = 0;
+    KC_CK(g, cudaMalloc(&g->d_ws, need));
+    g->ws_bytes = need;
+}
+
+// Pool growth (device arrays of per-tree values, optional parent arrays)
+template <class T>
+void grow(kc_graph *g, T *&p, int64_t old_count, int64_t new_cap, size_t per = 1) {
+    T *q = nullptr;
+    dalloc(g, &q, (size_t)new_cap * per);
+    if (p && old_count > 0)
+        KC_CK(g, cudaMemcpyAsync(q, p, sizeof(T) * (size_t)old_count * per,
+                                 cudaMemcpyDeviceToDevice, g->stream));
+    KC_CK(g, cudaStreamSynchronize(g->stream));
+    dfree(p);
+    p = q;
+}
+
+void ensure_pool(kc_graph *g, int64_t need) {
+    if (need <= g->pool_cap) return;
+    int64_t cap = std::max<int64_t>(need, std::max<int64_t>(1024, g->pool_cap * 2));
+    if (g->cfg.keep_trees) cap = need;  // parent arrays are large: grow exactly
+    grow(g, g->d_f, g->pool, cap);
+    grow(g, g->d_w, g->pool, cap);
+    grow(g, g->d_steps, g->pool, cap);
+    grow(g, g->d_sid, g->pool, cap);
+    if (g->cfg.keep_trees) grow(g, g->d_parents, g->pool, cap, (size_t)g->n);
+    g->pool_cap = cap;
+    g->h_modified.resize((size_t)cap, 0);
+}
+
+Plan plan_for(kc_graph *g, int64_t ntrees) {
+    Plan p;
+    p.bit = g->ttf_variant == KC_TTF_BIT;
+    size_t free_b = 0, total_b = 0;
+    KC_CK(g, cudaMemGetInfo(&free_b, &total_b));
+    const double frac = g->cfg.mem_fraction > 0 ? g->cfg.mem_fraction : 0.6;
+    const double budget = (double)(free_b + g->ws_bytes) * frac;
+    const double n = (double)g->n;
+    const double per_w = 12.0 * n + 64.0;
+    const double per_t = (p.bit ? 28.0 : 20.0) * n + 64.0 + (p.bit ? 16.0 * 4096.0 : 0.0);
+    int64_t bw = (int64_t)std::floor(0.7 * budget / per_w);
+    int64_t bt = (int64_t)std::floor(0.3 * budget / per_t);
+    bw = std::max<int64_t>(1, std::min<int64_t>(bw, ntrees));
+    if (g->cfg.max_trees_in_flight > 0) bw = std::min(bw, g->cfg.max_trees_in_flight);
+    bw = std::min<int64_t>(bw, 1 << 20);
+    bt = std::max<int64_t>(1, std::min<int64_t>(bt, bw));
+    bt = std::min<int64_t>(bt, 65535);
+    p.BW = bw;
+    p.BT = bt;
+    p.stack_cap = p.bit ? 4096 : 0;
+    return p;
+}
+
+// Per-tree cap on Wilson departures: the configured value, or
+// max(2^22, 1024 n) (about 60 times the mean step count of a road-shaped
+// graph, far above that of low-diameter graphs).
+int64_t step_cap_of(const kc_graph *g) {
+    if (g->cfg.step_cap > 0) return g->cfg.step_cap;
+    return std::max<int64_t>((int64_t)1 << 22, 1024 * g->n);
+}
+
+// One full sampling pass over sample ids [sid0, sid0 + B): walk, traverse,
+// evaluate f.  Leaves per-tree results in the carved workspace.
+void run_wave(kc_graph *g, Plan &p, int64_t B, int64_t sid0) {
+    GraphView gv = view_of(g);
+    Carved c = carve(g, p);
+    WaveView w = c.wv;
+    w.B = B;
+    KC_CK(g, cudaMemsetAsync(g->d_err, 0, 2 * sizeof(uint32_t), g->stream));
+    KC_CK(g, launch_iota(c.sids, sid0, B, g->stream));
+    {
+        Phase ph(g, g->t_wilson);
+        KC_CK(g, launch_wave_init(gv, w, g->stream));
+        KC_CK(g, launch_wilson(gv, w, g->seed, c.sids, step_cap_of(g), g->stream));
+        ph.done(2);
+    }
+    uint32_t hdr[2] = {0, 0};
+    KC_CK(g, cudaMemcpy(hdr, g->d_err, sizeof(hdr), cudaMemcpyDeviceToHost));
+    if (hdr[0] & kErrStepLimit) {
+        g->last_error = "Wilson walk exceeded the step cap";
+        throw Fail{KC_ERR_STEP_LIMIT};
+    }
+    if (p.bit) {
+        const int64_t need_cap = (int64_t)hdr[1] + 2;
+        if (need_cap > p.stack_cap) {
+            // re-carve with a larger stack; the Wilson results live in the
+            // leading regions, which keep their offsets only if the layout is
+            // unchanged, so grow into a fresh buffer and copy them across.
+            Plan q = p;
+            q.stack_cap = std::max<int64_t>(need_cap, p.stack_cap * 2);
+            const size_t need = ws_size(g, q);
+            if (need > g->ws_bytes) {
+                void *nb = nullptr;
+                KC_CK(g, cudaMalloc(&nb, need));
+                const size_t keep = align256(sizeof(uint64_t) * g->n * p.BW) +
+                                    align256(sizeof(int32_t) * g->n * p.BW) +
+                                    3 * align256(sizeof(int64_t) * p.BW);
+                KC_CK(g, cudaMemcpyAsync(nb, g->d_ws, keep, cudaMemcpyDeviceToDevice, g->stream));
+                KC_CK(g, cudaStreamSynchronize(g->stream));
+                dfree(g->d_ws);
+                g->d_ws = nb;
+                g->ws_bytes = need;
+            }
+            p = q;
+            c = carve(g, p);
+            w = c.wv;
+            w.B = B;
+        }
+    }
+    for (int64_t sub = 0; sub < B; sub += p.BT) {
+        const int64_t b = std::min<int64_t>(p.BT, B - sub);
+        WaveView s = w;
+        s.B = b;
+        s.word = w.word + sub * g->n;
+        s.ord = w.ord + sub * g->n;
+        s.steps = w.steps + sub;
+        s.f = w.f + sub;
+        {
+            Phase ph(g, g->t_traverse);
+            int nl = 0;
+            KC_CK(g, launch_traverse(gv, s, p.bit, g->stream, &nl));
+            ph.done(nl);
+        }
+        {
+            Phase ph(g, g->t_ttf);
+            if (p.bit) KC_CK(g, launch_ttf_bit(gv, s, g->stream));
+            else KC_CK(g, launch_ttf_scan(gv, s, g->stream));
+            ph.done(1);
+        }
+    }
+    KC_CK(g, cudaMemcpy(hdr, g->d_err, sizeof(hdr), cudaMemcpyDeviceToHost));
+    if (hdr[0] & kErrBadTree) {
+        g->last_error = "inconsistent tree state or traversal stack overflow";
+        throw Fail{KC_ERR_CUDA};
+    }
+}
+
+double inv_normal_upper(double p_upper) {
+    // z with P(Z > z) = p_upper, by bisection on erfc (monotone)
+    double lo = -40.0, hi = 40.0;
+    for (int i = 0; i < 200; ++i) {
+        const double mid = 0.5 * (lo + hi);
+        const double tail = 0.5 * std::erfc(mid / std::sqrt(2.0));
+        if (tail > p_upper) lo = mid; else hi = mid;
+    }
+    return 0.5 * (lo + hi);
+}
+
+double i128_to_double(long long hi, unsigned long long lo) {
+    return std::ldexp((double)hi, 64) + (double)lo;
+}
+
+PoolSums reduce_pool(kc_graph *g) {
+    PoolSums s{};
+    Phase ph(g, g->t_reduce);
+    KC_CK(g, launch_pool_reduce(g->d_f, g->d_w, g->pool, 2 * g->m, g->d_scratch, g->stream));
+    ph.done(1);
+    KC_CK(g, cudaMemcpy(&s, g->d_scratch, sizeof(s), cudaMemcpyDeviceToHost));
+    return s;
+}
+
+void do_sample(kc_graph *g, int64_t ntrees) {
+    if (ntrees <= 0) return;
+    ensure_pool(g, g->pool + ntrees);
+    Plan p = plan_for(g, ntrees);
+    ensure_ws(g, p);
+    const int64_t pool0 = g->pool, sid_base = g->next_sid;
+    int64_t done = 0;
+    try {
+        while (done < ntrees) {
+            const int64_t B = std::min<int64_t>(p.BW, ntrees - done);
+            run_wave(g, p, B, sid_base + done);
+            Carved c = carve(g, p);
+            WaveView w = c.wv;
+            w.B = B;
+            {
+                Phase ph(g, g->t_reduce);
+                KC_CK(g, launch_pool_append(w, g->pool, g->d_f, g->d_w, g->d_steps, g->d_sid,
+                                            c.sids, g->cfg.keep_trees ? g->d_parents : nullptr,
+                                            g->n, g->stream));
+                ph.done(g->cfg.keep_trees ? 2 : 1);
+            }
+            for (int64_t k = 0; k < B; ++k) g->h_modified[(size_t)(g->pool + k)] = 0;
+            g->pool += B;
+            done += B;
+            g->last_wave = B;
+        }
+    } catch (Fail &) {
+        g->pool = pool0;
+        g->next_sid = sid_base;
+        throw;
+    }
+    g->next_sid = sid_base + ntrees;
+}
+
+}  // namespace
+
+// =========================================================================
+// C ABI
+// =========================================================================
+extern "C" {
+
+void kc_config_default(kc_config *cfg) {
+    if (!cfg) return;
+    std::memset(cfg, 0, sizeof(*cfg));
+    cfg->struct_size = sizeof(kc_config);
+    cfg->root = -1;
+    cfg->ttf_variant = KC_TTF_AUTO;
+    cfg->keep_trees = 1;
+    cfg->stop_rule = KC_STOP_CLT;
+    cfg->refresh_after_update = 0;
+    cfg->inputs_on_device = 0;
+    cfg->r_source = KC_R_CG;
+    cfg->max_trees_in_flight = 0;
+    cfg->batch_trees = 1024;
+    cfg->max_trees = (int64_t)1 << 24;
+    cfg->step_cap = 0;
+    cfg->mem_fraction = 0.6;
+}
+
+const char *kc_status_string(kc_status s) {
+    switch (s) {
+        case KC_OK: return "ok";
+        case KC_ERR_INVALID_ARG: return "invalid argument";
+        case KC_ERR_NOT_SYMMETRIC: return "graph is not symmetric";
+        case KC_ERR_SELF_LOOP: return "graph has a self loop";
+        case KC_ERR_MULTI_EDGE: return "row not strictly ascending (repeated edge or unsorted)";
+        case KC_ERR_DISCONNECTED: return "graph is disconnected";
+        case KC_ERR_OVERFLOW: return "4 m^2 ecc(r) >= 2^62: f(tau) may overflow int64";
+        case KC_ERR_OUT_OF_MEMORY: return "device out of memory";
+        case KC_ERR_CUDA: return "CUDA error";
+        case KC_ERR_STEP_LIMIT: return "Wilson walk exceeded the step cap";
+        case KC_ERR_EDGE_EXISTS: return "inserted edge already exists";
+        case KC_ERR_EDGE_MISSING: return "deleted edge does not exist";
+        case KC_ERR_BRIDGE: return "deleted edge is a bridge";
+        case KC_ERR_NO_SAMPLES: return "no sampled trees";
+        case KC_ERR_NO_DEVICE: return "no sm_103 CUDA device";
+        case KC_ERR_NOT_RETAINED: return "trees were not retained (keep_trees = 0)";
+    }
+    return "unknown status";
+}
+
+const char *kc_last_error(kc_graph *g) { return g ? g->last_error.c_str() : ""; }
+
+kc_status kc_graph_destroy(kc_graph *g) {
+    if (!g) return KC_OK;
+    dfree(g->d_row_off);
+    dfree(g->d_col);
+    dfree(g->d_deg);
+    dfree(g->d_rec);
+    dfree(g->d_p0);
+    dfree(g->d_level0);
+    dfree(g->d_in0);
+    dfree(g->d_out0);
+    dfree(g->d_f);
+    dfree(g->d_w);
+    dfree(g->d_steps);
+    dfree(g->d_sid);
+    dfree(g->d_parents);
+    dfree(g->d_ws);
+    dfree(g->d_err);
+    if (g->d_scratch) cudaFree(g->d_scratch);
+    if (g->ev0) cudaEventDestroy(g->ev0);
+    if (g->ev1) cudaEventDestroy(g->ev1);
+    delete g;
+    return KC_OK;
+}
+
+kc_status kc_graph_create(int64_t n, const int64_t *row_off, const int32_t *col,
+                          const kc_config *cfg_in, kc_graph **out) {
+    if (!out) return KC_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (n < 2 || !row_off || !col) return KC_ERR_INVALID_ARG;
+    if (n > (int64_t)0x7FFFFFFF - 1) return KC_ERR_INVALID_ARG;
+    kc_config cfg;
+    kc_config_default(&cfg);
+    if (cfg_in) {
+        if (cfg_in->struct_size != sizeof(kc_config)) return KC_ERR_INVALID_ARG;
+        cfg = *cfg_in;
+    }
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+        (void)cudaGetLastError();
+        return KC_ERR_NO_DEVICE;
+    }
+    kc_graph *g = new (std::nothrow) kc_graph();
+    if (!g) return KC_ERR_OUT_OF_MEMORY;
+    g->cfg = cfg;
+    try {
+        KC_CK(g, cudaGetDevice(&g->device));
+        cudaDeviceProp prop;
+        KC_CK(g, cudaGetDeviceProperties(&prop, g->device));
+        if (prop.major != 10 || prop.minor != 3) {
+            g->last_error = "the library is built for sm_103a only";
+            throw Fail{KC_ERR_NO_DEVICE};
+        }
+        KC_CK(g, cudaEventCreate(&g->ev0));
+        KC_CK(g, cudaEventCreate(&g->ev1));
+        g->n = n;
+        // host copy of the CSR (validated layout, kept for updates)
+        g->h_row_off.resize((size_t)n + 1);
+        const cudaMemcpyKind kind = cfg.inputs_on_device ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost;
+        KC_CK(g, cudaMemcpy(g->h_row_off.data(), row_off, sizeof(int64_t) * (n + 1), kind));
+        if (g->h_row_off[0] != 0) throw Fail{KC_ERR_INVALID_ARG};
+        for (int64_t v = 0; v < n; ++v)
+            if (g->h_row_off[v + 1] < g->h_row_off[v]) throw Fail{KC_ERR_INVALID_ARG};
+        const int64_t twom = g->h_row_off[n];
+        if (twom % 2 != 0 || twom == 0) throw Fail{twom == 0 ? KC_ERR_DISCONNECTED : KC_ERR_NOT_SYMMETRIC};
+        g->m = twom / 2;
+        g->h_col.resize((size_t)twom);
+        KC_CK(g, cudaMemcpy(g->h_col.data(), col, sizeof(int32_t) * twom, kind));
+
+        dalloc(g, &g->d_row_off, n + 1);
+        dalloc(g, &g->d_col, twom);
+        dalloc(g, &g->d_deg, n);
+        dalloc(g, &g->d_rec, n);
+        dalloc(g, &g->d_p0, n);
+        dalloc(g, &g->d_level0, n);
+        dalloc(g, &g->d_in0, n);
+        dalloc(g, &g->d_out0, n);
+        dalloc(g, &g->d_err, 4);
+        g->scratch_bytes = 4096;
+        KC_CK(g, cudaMalloc(&g->d_scratch, g->scratch_bytes));
+        KC_CK(g, cudaMemcpyAsync(g->d_row_off, g->h_row_off.data(), sizeof(int64_t) * (n + 1),
+                                 cudaMemcpyHostToDevice, g->stream));
+        KC_CK(g, cudaMemcpyAsync(g->d_col, g->h_col.data(), sizeof(int32_t) * twom,
+                                 cudaMemcpyHostToDevice, g->stream));
+
+        Phase ph(g, g->t_setup);
+        int launches = 0;
+        GraphView gv = view_of(g);
+        KC_CK(g, launch_build_records(gv, g->d_rec, g->d_deg, g->stream));
+        ++launches;
+        uint32_t *d_flags = g->d_err;
+        KC_CK(g, cudaMemsetAsync(d_flags, 0, 4 * sizeof(uint32_t), g->stream));
+        KC_CK(g, launch_validate(gv, d_flags, g->stream));
+        ++launches;
+        uint32_t flags = 0;
+        KC_CK(g, cudaMemcpyAsync(&flags, d_flags, sizeof(flags), cudaMemcpyDeviceToHost, g->stream));
+        KC_CK(g, cudaStreamSynchronize(g->stream));
+        if (flags & 1u) throw Fail{KC_ERR_INVALID_ARG};
+        if (flags & 2u) throw Fail{KC_ERR_SELF_LOOP};
+        if (flags & 4u) throw Fail{KC_ERR_MULTI_EDGE};
+        if (flags & 8u) throw Fail{KC_ERR_NOT_SYMMETRIC};
+        if (flags & 16u) throw Fail{KC_ERR_DISCONNECTED};
+
+        // root
+        if (cfg.root >= 0) {
+            if (cfg.root >= n) throw Fail{KC_ERR_INVALID_ARG};
+            g->root = cfg.root;
+        } else {
+            unsigned long long *d_best = (unsigned long long *)g->d_scratch;
+            KC_CK(g, cudaMemsetAsync(d_best, 0, sizeof(unsigned long long), g->stream));
+            KC_CK(g, launch_root(gv, d_best, g->stream));
+            ++launches;
+            unsigned long long best = 0;
+            KC_CK(g, cudaMemcpyAsync(&best, d_best, sizeof(best), cudaMemcpyDeviceToHost, g->stream));
+            KC_CK(g, cudaStreamSynchronize(g->stream));
+            g->root = (int32_t)(0xFFFFFFFFull - (best & 0xFFFFFFFFull));
+        }
+        gv.root = g->root;
+        // BFS levels, one launch per level
+        KC_CK(g, launch_bfs_init(n, g->root, g->d_level0, g->stream));
+        ++launches;
+        int32_t *d_changed = (int32_t *)g->d_scratch;
+        int32_t lev = 0;
+        for (;; ++lev) {
+            KC_CK(g, cudaMemsetAsync(d_changed, 0, sizeof(int32_t), g->stream));
+            KC_CK(g, launch_bfs_level(gv, lev, g->d_level0, d_changed, g->stream));
+            ++launches;
+            int32_t changed = 0;
+            KC_CK(g, cudaMemcpyAsync(&changed, d_changed, sizeof(changed), cudaMemcpyDeviceToHost,
+                                     g->stream));
+            KC_CK(g, cudaStreamSynchronize(g->stream));
+            if (!changed) break;
+            if (lev > n) throw Fail{KC_ERR_CUDA};
+        }
+        g->ecc = lev;
+        gv.ecc = lev;
+        int32_t *d_unreached = (int32_t *)g->d_scratch;
+        KC_CK(g, cudaMemsetAsync(d_unreached, 0, sizeof(int32_t), g->stream));
+        KC_CK(g, launch_bfs_parent(gv, g->d_level0, g->d_p0, d_unreached, g->stream));
+        ++launches;
+        int32_t unreached = 0;
+        KC_CK(g, cudaMemcpyAsync(&unreached, d_unreached, sizeof(int32_t), cudaMemcpyDeviceToHost,
+                                 g->stream));
+        KC_CK(g, cudaStreamSynchronize(g->stream));
+        if (unreached) throw Fail{KC_ERR_DISCONNECTED};
+        // overflow margin: |f| <= 4 m^2 ecc (Theorem 5's proof) must stay below 2^62
+        {
+            const long double bound = 4.0L * (long double)g->m * (long double)g->m * (long double)g->ecc;
+            if (bound >= 4611686018427387904.0L) throw Fail{KC_ERR_OVERFLOW};
+        }
+        // tau0 traversal with the same passes as the sampled trees (B = 1)
+        {
+            Plan p;
+            p.BW = 1;
+            p.BT = 1;
+            ensure_ws(g, p);
+            Carved c = carve(g, p);
+            WaveView w = c.wv;
+            w.B = 1;
+            KC_CK(g, launch_tau0_words(n, g->d_p0, g->d_level0, w.word, g->stream));
+            KC_CK(g, launch_level_order(n, g->ecc, g->d_level0, w.din, w.ord, g->stream));
+            int nl = 0;
+            KC_CK(g, launch_traverse(gv, w, false, g->stream, &nl));
+            KC_CK(g, launch_out_from_size(n, w.din, w.size, g->d_out0, g->stream));
+            KC_CK(g, cudaMemcpyAsync(g->d_in0, w.din, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice,
+                                     g->stream));
+            launches += 4 + nl;
+        }
+        ph.done(launches);
+        // TTF variant (Theorem 8: O(n min(Delta, log n)))
+        int lg = 0;
+        while (((int64_t)1 << lg) < n) ++lg;
+        int variant = cfg.ttf_variant;
+        if (variant == KC_TTF_AUTO) variant = (g->ecc <= 2 * lg) ? KC_TTF_SCAN : KC_TTF_BIT;
+        if (variant == KC_TTF_BIT && twom >= ((int64_t)1 << 31)) variant = KC_TTF_SCAN;
+        g->ttf_variant = variant;
+    } catch (Fail &f) {
+        kc_graph_destroy(g);
+        return f.st;
+    }
+    *out = g;
+    return KC_OK;
+}
+
+kc_status kc_graph_set_stream(kc_graph *g, void *cuda_stream) {
+    if (!g) return KC_ERR_INVALID_ARG;
+    g->stream = (cudaStream_t)cuda_stream;
+    return KC_OK;
+}
+
+kc_status kc_sample(kc_graph *g, uint64_t seed, int64_t n_trees) {
+    if (!g || n_trees < 0) return KC_ERR_INVALID_ARG;
+    if (g->seeded && seed != g->seed) {
+        g->last_error = "kc_sample: the handle is already seeded with a different seed";
+        return KC_ERR_INVALID_ARG;
+    }
+    if (n_trees == 0) return KC_OK;
+    const bool was_seeded = g->seeded;
+    g->seed = seed;
+    g->seeded = true;
+    try {
+        do_sample(g, n_trees);
+    } catch (Fail &f) {
+        g->seeded = was_seeded;
+        return f.st;
+    }
+    return KC_OK;
+}
+
+kc_status kc_estimate(kc_graph *g, double eps, double delta, double *K_out) {
+    if (!g || !K_out) return KC_ERR_INVALID_ARG;
+    if (eps > 0 && !(delta > 0 && delta < 1)) return KC_ERR_INVALID_ARG;
+    try {
+        if (!g->seeded) {
+            g->seed = 0;
+            g->seeded = true;
+        }
+        const int64_t cap = g->cfg.max_trees > 0 ? g->cfg.max_trees : ((int64_t)1 << 24);
+        const int64_t batch = g->cfg.batch_trees > 0 ? g->cfg.batch_trees : 1024;
+        if (eps > 0) {
+            if (g->cfg.stop_rule == KC_STOP_HOEFFDING) {
+                const double nn = (double)g->n, mm = (double)g->m, e = (double)g->ecc;
+                const double kmin = (nn - 1) * (nn - 1) / nn;
+                const double need = std::ceil(8.0 * mm * mm * e * e * std::log(2.0 / delta) /
+                                              (kmin * kmin * eps * eps));
+                const int64_t want = (int64_t)std::min<double>(need, (double)cap);
+                if (want > g->pool) do_sample(g, want - g->pool);
+            } else {
+                const double z = inv_normal_upper(delta / 2.0);
+                if (g->pool < 64) do_sample(g, std::max<int64_t>(64, std::min(batch, cap)) - g->pool);
+                for (int iter = 0; iter < 64; ++iter) {
+                    PoolSums s = reduce_pool(g);
+                    const double w = (double)s.count;
+                    const double mean = s.wf / s.w;
+                    const double var = std::max(0.0, (s.x2 - w * mean * mean) / std::max(1.0, w - 1.0));
+                    const double sd = std::sqrt(var);
+                    const double tol = eps * mean * (1.0 - eps);
+                    if (w >= 64 && z * sd / std::sqrt(w) <= tol) break;
+                    if (g->pool >= cap) break;
+                    double need = tol > 0 ? std::ceil((z * sd / tol) * (z * sd / tol)) : (double)cap;
+                    int64_t more = (int64_t)std::min<double>(std::max<double>(need - w, (double)batch),
+                                                             (double)(cap - g->pool));
+                    if (more <= 0) break;
+                    do_sample(g, more);
+                }
+            }
+        }
+        if (g->pool == 0) return KC_ERR_NO_SAMPLES;
+        PoolSums s = reduce_pool(g);
+        bool unit = true;
+        for (int64_t k = 0; k < g->pool && unit; ++k) unit = !g->h_modified[(size_t)k];
+        if (unit && s.w == (double)s.count) {
+            *K_out = i128_to_double(s.f_hi, s.f_lo) / ((double)(2 * g->m) * (double)s.count);
+        } else {
+            *K_out = s.wf / s.w;
+        }
+    } catch (Fail &f) {
+        return f.st;
+    }
+    return KC_OK;
+}
+
+kc_status kc_get_samples(kc_graph *g, int64_t first, int64_t count, int64_t *f, double *weight,
+                         int64_t *steps, int64_t *sample_id) {
+    if (!g || first < 0 || count < 0 || first + count > g->pool) return KC_ERR_INVALID_ARG;
+    if (count == 0) return KC_OK;
+    try {
+        if (f) KC_CK(g, cudaMemcpyAsync(f, g->d_f + first, sizeof(int64_t) * count, cudaMemcpyDeviceToHost, g->stream));
+        if (weight) KC_CK(g, cudaMemcpyAsync(weight, g->d_w + first, sizeof(double) * count, cudaMemcpyDeviceToHost, g->stream));
+        if (steps) KC_CK(g, cudaMemcpyAsync(steps, g->d_steps + first, sizeof(int64_t) * count, cudaMemcpyDeviceToHost, g->stream));
+        if (sample_id) KC_CK(g, cudaMemcpyAsync(sample_id, g->d_sid + first, sizeof(int64_t) * count, cudaMemcpyDeviceToHost, g->stream));
+        KC_CK(g, cudaStreamSynchronize(g->stream));
+    } catch (Fail &e) {
+        return e.st;
+    }
+    return KC_OK;
+}
+
+kc_status kc_get_tau0(kc_graph *g, int32_t *p0, int32_t *level, int32_t *in0, int32_t *out0,
+                      int32_t *root, int32_t *ecc) {
+    if (!g) return KC_ERR_INVALID_ARG;
+    try {
+        const size_t b = sizeof(int32_t) * (size_t)g->n;
+        if (p0) KC_CK(g, cudaMemcpyAsync(p0, g->d_p0, b, cudaMemcpyDeviceToHost, g->stream));
+        if (level) KC_CK(g, cudaMemcpyAsync(level, g->d_level0, b, cudaMemcpyDeviceToHost, g->stream));
+        if (in0) KC_CK(g, cudaMemcpyAsync(in0, g->d_in0, b, cudaMemcpyDeviceToHost, g->stream));
+        if (out0) KC_CK(g, cudaMemcpyAsync(out0, g->d_out0, b, cudaMemcpyDeviceToHost, g->stream));
+        KC_CK(g, cudaStreamSynchronize(g->stream));
+        if (root) *root = g->root;
+        if (ecc) *ecc = g->ecc;
+    } catch (Fail &e) {
+        return e.st;
+    }
+    return KC_OK;
+}
+
+kc_status kc_get_tree(kc_graph *g, int64_t sample, int32_t *parent, int32_t *depth,
+                      int32_t *dfn_in, int32_t *dfn_out, int64_t *vol, int64_t *f,
+                      int64_t *steps) {
+    if (!g || sample < 0 || sample >= g->pool) return KC_ERR_INVALID_ARG;
+    if (g->h_modified[(size_t)sample]) return KC_ERR_NOT_RETAINED;
+    try {
+        int64_t sid = 0;
+        KC_CK(g, cudaMemcpy(&sid, g->d_sid + sample, sizeof(int64_t), cudaMemcpyDeviceToHost));
+        Plan p;
+        p.BW = 1;
+        p.BT = 1;
+        p.bit = g->ttf_variant == KC_TTF_BIT;
+        p.stack_cap = p.bit ? 4096 : 0;
+        ensure_ws(g, p);
+        run_wave(g, p, 1, sid);
+        Carved c = carve(g, p);
+        const int64_t n = g->n;
+        std::vector<uint64_t> word((size_t)n);
+        std::vector<int32_t> din((size_t)n), size((size_t)n);
+        KC_CK(g, cudaMemcpy(word.data(), c.wv.word, sizeof(uint64_t) * n, cudaMemcpyDeviceToHost));
+        KC_CK(g, cudaMemcpy(din.data(), c.wv.din, sizeof(int32_t) * n, cudaMemcpyDeviceToHost));
+        KC_CK(g, cudaMemcpy(size.data(), c.wv.size, sizeof(int32_t) * n, cudaMemcpyDeviceToHost));
+        if (vol) KC_CK(g, cudaMemcpy(vol, c.wv.vol, sizeof(int64_t) * n, cudaMemcpyDeviceToHost));
+        if (f) KC_CK(g, cudaMemcpy(f, c.wv.f, sizeof(int64_t), cudaMemcpyDeviceToHost));
+        if (steps) KC_CK(g, cudaMemcpy(steps, c.wv.steps, sizeof(int64_t), cudaMemcpyDeviceToHost));
+        for (int64_t v = 0; v < n; ++v) {
+            if (parent) parent[v] = w_next(word[(size_t)v]);
+            if (depth) depth[v] = (int32_t)w_count(word[(size_t)v]);
+            if (dfn_in) dfn_in[v] = din[(size_t)v];
+            if (dfn_out) dfn_out[v] = din[(size_t)v] + size[(size_t)v] - 1;
+        }
+    } catch (Fail &e) {
+        return e.st;
+    }
+    return KC_OK;
+}
+
+kc_status kc_stats(kc_graph *g, kc_stats_t *out) {
+    if (!g || !out) return KC_ERR_INVALID_ARG;
+    std::memset(out, 0, sizeof(*out));
+    out->n = g->n;
+    out->m = g->m;
+    out->root = g->root;
+    out->ecc = g->ecc;
+    out->ttf_variant = g->ttf_variant;
+    out->pool_trees = g->pool;
+    out->next_sample_id = g->next_sid;
+    out->trees_in_flight = g->last_wave;
+    out->pool_bytes = g->pool_cap * (int64_t)(8 + 8 + 8 + 8) +
+                      (g->cfg.keep_trees ? g->pool_cap * g->n * 4 : 0);
+    out->workspace_bytes = (int64_t)g->ws_bytes;
+    out->updates_applied = g->updates_applied;
+    out->trees_resampled = g->trees_resampled;
+    out->ms_wilson = g->t_wilson.ms;
+    out->ms_traverse = g->t_traverse.ms;
+    out->ms_ttf = g->t_ttf.ms;
+    out->ms_reduce = g->t_reduce.ms;
+    out->ms_update = g->t_update.ms;
+    out->ms_setup = g->t_setup.ms;
+    out->launches_wilson = g->t_wilson.launches;
+    out->launches_traverse = g->t_traverse.launches;
+    out->launches_ttf = g->t_ttf.launches;
+    out->launches_reduce = g->t_reduce.launches;
+    out->launches_update = g->t_update.launches;
+    out->launches_setup = g->t_setup.launches;
+    if (g->pool > 0) {
+        try {
+            std::vector<int64_t> st((size_t)g->pool);
+            KC_CK(g, cudaMemcpy(st.data(), g->d_steps, sizeof(int64_t) * g->pool,
+                                cudaMemcpyDeviceToHost));
+            int64_t tot = 0;
+            for (int64_t x : st) tot += x;
+            out->total_steps = tot;
+            PoolSums s{};
+            KC_CK(g, launch_pool_reduce(g->d_f, g->d_w, g->pool, 2 * g->m, g->d_scratch, g->stream));
+            KC_CK(g, cudaMemcpy(&s, g->d_scratch, sizeof(s), cudaMemcpyDeviceToHost));
+            out->f_sum_hi = s.f_hi;
+            out->f_sum_lo = s.f_lo;
+            out->wf_sum = s.wf;
+            out->w_sum = s.w;
+            out->x2_sum = s.x2;
+        } catch (Fail &e) {
+            return e.st;
+        }
+    }
+    return KC_OK;
+}
+
+kc_status kc_reset_timers(kc_graph *g) {
+    if (!g) return KC_ERR_INVALID_ARG;
+    g->t_wilson = g->t_traverse = g->t_ttf = g->t_reduce = g->t_update = g->t_setup = PhaseTimer();
+    return KC_OK;
+}
+
+kc_status kc_update(kc_graph *g, const kc_edge_op *ops, int64_t n_ops, int32_t mode) {
+    if (!g || (n_ops > 0 && !ops) || n_ops < 0) return KC_ERR_INVALID_ARG;
+    if (mode != KC_UPDATE_BSM && mode != KC_UPDATE_ISM) return KC_ERR_INVALID_ARG;
+    g->last_error = "kc_update: not available in this build";
+    return KC_ERR_INVALID_ARG;
+}
+
+}  // extern "C"

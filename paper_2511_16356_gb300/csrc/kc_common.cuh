@@ -1,0 +1,238 @@
+// Internal declarations shared by the CUDA translation units of libkc.
+// Layout of every device array is documented where it is declared.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/kc.h"
+
+namespace kc {
+
+// ---------------------------------------------------------------------------
+// Random-number contract: Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11),
+// key = (seed lo, seed hi), counter = (c0, c1, c2, tag << 24 | retry), and
+// Lemire's multiply-and-reject bounded integers over the block's four words.
+// ---------------------------------------------------------------------------
+constexpr uint32_t kPhiloxM0 = 0xD2511F53u;
+constexpr uint32_t kPhiloxM1 = 0xCD9E8D57u;
+constexpr uint32_t kPhiloxW0 = 0x9E3779B9u;
+constexpr uint32_t kPhiloxW1 = 0xBB67AE85u;
+
+constexpr uint32_t kTagWalk = 0u;     // Wilson departures: (u, k, sample id)
+constexpr uint32_t kTagSelect = 1u;   // update: choice of trees to replace / transform
+constexpr uint32_t kTagLinkCut = 2u;  // ISM insert: edge of the cycle to cut
+constexpr uint32_t kTagCutLink = 3u;  // ISM delete: crossing edge to link
+
+__device__ __forceinline__ void philox4x32_10(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                              uint32_t k0, uint32_t k1, uint32_t out[4]) {
+#pragma unroll
+    for (int i = 0; i < 10; ++i) {
+        const uint32_t lo0 = kPhiloxM0 * c0;
+        const uint32_t hi0 = __umulhi(kPhiloxM0, c0);
+        const uint32_t lo1 = kPhiloxM1 * c2;
+        const uint32_t hi1 = __umulhi(kPhiloxM1, c2);
+        c0 = hi1 ^ c1 ^ k0;
+        c1 = lo1;
+        c2 = hi0 ^ c3 ^ k1;
+        c3 = lo0;
+        k0 += kPhiloxW0;
+        k1 += kPhiloxW1;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+// Uniform integer in [0, s), s >= 1.
+__device__ __forceinline__ uint32_t bounded_draw(uint64_t seed, uint32_t c0, uint32_t c1,
+                                                 uint32_t c2, uint32_t tag, uint32_t s) {
+    const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+    for (uint32_t retry = 0; retry < (1u << 24); ++retry) {
+        uint32_t w[4];
+        philox4x32_10(c0, c1, c2, (tag << 24) | retry, k0, k1, w);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const uint64_t m = (uint64_t)w[j] * (uint64_t)s;
+            const uint32_t low = (uint32_t)m;
+            if (low < s) {  // only then can the rejection threshold matter
+                const uint32_t thr = (0u - s) % s;
+                if (low < thr) continue;
+            }
+            return (uint32_t)(m >> 32);
+        }
+    }
+    return 0;
+}
+
+// ---------------------------------------------------------------------------
+// Vertex record used by the walk: one 32-byte sector per vertex holding the
+// degree, the CSR offset and the first kInline neighbours, so a step on a
+// vertex of degree <= kInline costs one sector of graph data.
+// ---------------------------------------------------------------------------
+constexpr int kInline = 5;
+struct __align__(32) VRec {
+    int32_t deg;
+    uint32_t off_lo;
+    uint32_t off_hi;
+    int32_t nbr[kInline];
+};
+static_assert(sizeof(VRec) == 32, "VRec must be one sector");
+
+// ---------------------------------------------------------------------------
+// Per-tree vertex word of the walker (8 bytes):
+//   bits  0..31  next / parent (int32; -1 for the root)
+//   bits 32..62  departure count while the vertex is outside the tree,
+//                depth once it is in the tree
+//   bit  63      in-tree flag
+// ---------------------------------------------------------------------------
+constexpr uint64_t kInTree = 1ull << 63;
+__host__ __device__ __forceinline__ int32_t w_next(uint64_t w) { return (int32_t)(uint32_t)w; }
+__host__ __device__ __forceinline__ uint32_t w_count(uint64_t w) {
+    return (uint32_t)(w >> 32) & 0x7FFFFFFFu;
+}
+__host__ __device__ __forceinline__ bool w_in_tree(uint64_t w) { return (w & kInTree) != 0; }
+__host__ __device__ __forceinline__ uint64_t w_make(int32_t next, uint32_t count, bool in_tree) {
+    return (uint64_t)(uint32_t)next | ((uint64_t)(count & 0x7FFFFFFFu) << 32) |
+           (in_tree ? kInTree : 0ull);
+}
+
+// Error word bits written by kernels (read back by the host after a phase).
+constexpr uint32_t kErrStepLimit = 1u;
+constexpr uint32_t kErrBadTree = 2u;
+constexpr uint32_t kErrIterLimit = 4u;
+
+// ---------------------------------------------------------------------------
+// Device views
+// ---------------------------------------------------------------------------
+struct GraphView {
+    int64_t n;
+    int64_t twom;
+    const int64_t *row_off;  // [n+1]
+    const int32_t *col;      // [2m]
+    const int32_t *deg;      // [n]
+    const VRec *rec;         // [n]
+    int32_t root;
+    int32_t ecc;
+    const int32_t *p0;       // [n] tau0 parent, -1 at the root
+    const int32_t *in0;      // [n] tau0 DFN
+    const int32_t *out0;     // [n]
+};
+
+// Workspace of one wave of B trees; every per-tree array is tree-major
+// ([tree][vertex], tree stride = n).
+struct WaveView {
+    int64_t B;               // trees in this wave
+    int64_t n;
+    uint64_t *word;          // [B][n] walker words (parent + depth afterwards)
+    int32_t *ord;            // [B][n] parent-first order from the walk (root first);
+                             // reused as the DFS stack by the BIT variant
+    int32_t *size;           // [B][n] subtree sizes
+    int64_t *vol;            // [B][n] subtree volumes
+    int32_t *din;            // [B][n] DFN (sibling offsets before the top-down pass)
+    int32_t *aux;            // [B][n] per-parent running sums, then preorder (BIT variant)
+    int64_t *bit;            // [B][n+1] Fenwick array (BIT variant), may be null
+    int64_t *steps;          // [B]
+    int64_t *f;              // [B]
+    uint32_t *err;           // [1] error bits (kErr*)
+    int32_t *maxdepth;       // [1] largest tree depth seen in the wave
+    int32_t *stack;          // [B][stack_cap] x 4 int32 DFS stack (BIT variant)
+    int64_t stack_cap;       // entries per tree
+};
+
+// ---------------------------------------------------------------------------
+// Host handle
+// ---------------------------------------------------------------------------
+struct PhaseTimer {
+    double ms = 0.0;
+    int64_t launches = 0;
+};
+
+}  // namespace kc
+
+struct kc_graph {
+    kc_config cfg;
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int64_t n = 0, m = 0;
+    // device graph
+    int64_t *d_row_off = nullptr;
+    int32_t *d_col = nullptr;
+    int32_t *d_deg = nullptr;
+    kc::VRec *d_rec = nullptr;
+    int32_t root = -1, ecc = 0;
+    int32_t *d_p0 = nullptr, *d_level0 = nullptr, *d_in0 = nullptr, *d_out0 = nullptr;
+    int32_t ttf_variant = KC_TTF_SCAN;
+    // host copy of the graph (validated CSR, needed by updates)
+    std::vector<int64_t> h_row_off;
+    std::vector<int32_t> h_col;
+    // pool
+    bool seeded = false;
+    uint64_t seed = 0;
+    int64_t pool = 0, pool_cap = 0;
+    int64_t next_sid = 0;
+    int64_t *d_f = nullptr;
+    double *d_w = nullptr;
+    int64_t *d_steps = nullptr;
+    int64_t *d_sid = nullptr;
+    int32_t *d_parents = nullptr;  // [pool_cap][n] when keep_trees
+    std::vector<uint8_t> h_modified; // tree changed by an update (not reproducible from its id)
+    // workspace
+    void *d_ws = nullptr;
+    size_t ws_bytes = 0;
+    int64_t ws_trees = 0;
+    uint32_t *d_err = nullptr;
+    void *d_scratch = nullptr;      // small reduction scratch
+    size_t scratch_bytes = 0;
+    int64_t last_wave = 0;
+    int64_t total_steps = 0;
+    int64_t updates_applied = 0, trees_resampled = 0;
+    int64_t update_seq = 0;
+    kc::PhaseTimer t_wilson, t_traverse, t_ttf, t_reduce, t_update, t_setup;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    std::string last_error;
+};
+
+namespace kc {
+
+// Launch helpers implemented in the .cu files.  Each returns cudaGetLastError().
+cudaError_t launch_build_records(const GraphView &g, VRec *rec, int32_t *deg, cudaStream_t s);
+cudaError_t launch_validate(const GraphView &g, uint32_t *flags, cudaStream_t s);
+cudaError_t launch_root(const GraphView &g, unsigned long long *best, cudaStream_t s);
+cudaError_t launch_bfs_init(int64_t n, int32_t r, int32_t *level, cudaStream_t s);
+cudaError_t launch_bfs_level(const GraphView &g, int32_t lev, int32_t *level, int32_t *changed,
+                             cudaStream_t s);
+cudaError_t launch_bfs_parent(const GraphView &g, const int32_t *level, int32_t *p0,
+                              int32_t *unreached, cudaStream_t s);
+cudaError_t launch_tau0_words(int64_t n, const int32_t *p0, const int32_t *level, uint64_t *word,
+                              cudaStream_t s);
+cudaError_t launch_level_order(int64_t n, int32_t ecc, const int32_t *level, int32_t *hist,
+                               int32_t *ord, cudaStream_t s);
+
+cudaError_t launch_wave_init(const GraphView &g, WaveView w, cudaStream_t s);
+cudaError_t launch_wilson(const GraphView &g, WaveView w, uint64_t seed, const int64_t *sids,
+                          int64_t step_cap, cudaStream_t s);
+cudaError_t launch_traverse(const GraphView &g, WaveView w, bool want_preorder, cudaStream_t s,
+                            int *launches);
+cudaError_t launch_ttf_scan(const GraphView &g, WaveView w, cudaStream_t s);
+cudaError_t launch_ttf_bit(const GraphView &g, WaveView w, cudaStream_t s);
+cudaError_t launch_pool_append(WaveView w, int64_t first, int64_t *pool_f, double *pool_w,
+                               int64_t *pool_steps, int64_t *pool_sid, const int64_t *sids,
+                               int32_t *pool_parents, int64_t n, cudaStream_t s);
+cudaError_t launch_pool_reduce(const int64_t *f, const double *w, int64_t count, int64_t twom,
+                               void *scratch, cudaStream_t s);
+cudaError_t launch_words_from_parents(int64_t n, int64_t B, const int32_t *parents,
+                                      uint64_t *word, cudaStream_t s);
+
+// Result layout of launch_pool_reduce in `scratch`.
+struct PoolSums {
+    long long f_hi;          // int128 sum of f as (hi, lo) limbs
+    unsigned long long f_lo;
+    double wf;               // sum w f / 2m
+    double w;                // sum w
+    double x2;               // sum (f / 2m)^2 (unit weights)
+    long long count;
+};
+
+}  // namespace kc

@@ -1,0 +1,203 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle on the
+same seeded inputs and the same Philox streams.
+
+Integer outputs (tau0, parent, depth, DFN, subtree volume, Wilson step count and
+f(tau)) must match bit for bit; K_hat is compared with 1e-12 relative
+tolerance (it is a division of the same exact integer sum) and, against the
+exact Kemeny constant, within the requested relative error.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2511_16356_gb300 import synth as S
+
+pytestmark = pytest.mark.gpu
+
+kc = pytest.importorskip("paper_2511_16356_gb300.kc")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2511_16356_gb300 import build as kbuild
+
+    kbuild.build()
+    kc.load()
+
+
+def _cfg(variant=kc.KC_TTF_AUTO, **kw):
+    c = kc.kc_config_default()
+    c.ttf_variant = variant
+    for k, v in kw.items():
+        setattr(c, k, v)
+    return c
+
+
+SMALL = {
+    "er300": lambda: S.er_lcc(300, 0.02, 7),
+    "grid17x13": lambda: S.grid_perturbed(17, 13, 0.25, 3),
+    "K7": lambda: S.complete(7),
+    "C40": lambda: S.cycle(40),
+    "star9": lambda: S.star(9),
+    "path33": lambda: S.path(33),
+    "K3,5": lambda: S.complete_bipartite(3, 5),
+    "cl3000": lambda: S.chung_lu(3000, 2.1, 8.0, 5),
+}
+
+
+@pytest.mark.parametrize("name", list(SMALL))
+def test_tau0_matches_oracle(name):
+    g = SMALL[name]()
+    t0 = O.tau0(g)
+    with kc.KemenyGraph.from_graph(g) as G:
+        tau = G.tau0()
+        assert tau["root"] == t0.r
+        assert tau["ecc"] == t0.ecc
+        assert np.array_equal(tau["p0"], t0.p0)
+        assert np.array_equal(tau["level"], t0.level)
+        assert np.array_equal(tau["in0"], t0.in0)
+        assert np.array_equal(tau["out0"], t0.out0)
+
+
+@pytest.mark.parametrize("variant", [kc.KC_TTF_SCAN, kc.KC_TTF_BIT])
+@pytest.mark.parametrize("name", list(SMALL))
+def test_trees_bit_exact(name, variant):
+    g = SMALL[name]()
+    t0 = O.tau0(g)
+    seed = 4242
+    ntrees = 200
+    with kc.KemenyGraph.from_graph(g, _cfg(variant)) as G:
+        G.sample(seed, ntrees)
+        got = G.samples()
+        f_ref, st_ref = O.sample_batch(g, t0, seed, 0, ntrees)
+        assert np.array_equal(got["sid"], np.arange(ntrees))
+        assert np.array_equal(got["steps"], st_ref)
+        assert np.array_equal(got["f"], f_ref)
+        for k in [0, 1, ntrees // 2, ntrees - 1]:
+            tr = G.tree(k)
+            ref = O.tree(g, t0, seed, k)
+            assert np.array_equal(tr["parent"], ref.parent)
+            assert np.array_equal(tr["depth"], ref.depth)
+            assert np.array_equal(tr["din"], ref.din)
+            assert np.array_equal(tr["dout"], ref.dout)
+            assert np.array_equal(tr["vol"], ref.vol)
+            assert tr["f"] == ref.f and tr["steps"] == ref.steps
+
+
+def test_launch_shape_does_not_change_trees():
+    """Trees depend on (seed, sample id) only: one tree in flight or all of them,
+    and sampling in several calls, give the same pool."""
+    g = S.er_lcc(400, 0.015, 11)
+    with kc.KemenyGraph.from_graph(g) as A, \
+            kc.KemenyGraph.from_graph(g, _cfg(max_trees_in_flight=1)) as B:
+        A.sample(9, 64)
+        for _ in range(4):
+            B.sample(9, 16)
+        a, b = A.samples(), B.samples()
+        assert np.array_equal(a["f"], b["f"]) and np.array_equal(a["steps"], b["steps"])
+
+
+def test_estimate_equals_exact_integer_mean():
+    g = S.er_lcc(500, 0.01, 2)
+    t0 = O.tau0(g)
+    with kc.KemenyGraph.from_graph(g) as G:
+        G.sample(3, 300)
+        k = G.estimate()
+        f_ref, _ = O.sample_batch(g, t0, 3, 0, 300)
+        want = float(int(f_ref.sum())) / (2 * g.m * 300)
+        assert k == pytest.approx(want, rel=1e-12)
+        st = G.stats()
+        assert st["f_sum_hi"] * (1 << 64) + st["f_sum_lo"] == sum(int(x) for x in f_ref)
+
+
+def test_er2000_full_config_parity_and_accuracy():
+    """The small static configuration: ER G(2000, 8/1999) LCC, 2000 trees; every
+    tree bit-exact, K within 1% of the FP64 eigendecomposition."""
+    g = S.workload("er2000")
+    t0 = O.tau0(g)
+    k_exact = O.K_dense(g)
+    with kc.KemenyGraph.from_graph(g) as G:
+        G.sample(0, 2000)
+        got = G.samples()
+        f_ref, st_ref = O.sample_batch(g, t0, 0, 0, 2000)
+        assert np.array_equal(got["f"], f_ref)
+        assert np.array_equal(got["steps"], st_ref)
+        k = G.estimate()
+        assert abs(k - k_exact) / k_exact < 0.01
+
+
+def test_estimate_to_eps_covers_exact():
+    g = S.er_lcc(800, 0.01, 4)
+    k_exact = O.K_dense(g)
+    misses = 0
+    for seed in range(8):
+        with kc.KemenyGraph.from_graph(g) as G:
+            G.sample(seed, 64)
+            k = G.estimate(0.01, 0.05)
+            misses += abs(k - k_exact) > 0.01 * k_exact
+    assert misses <= 2
+
+
+@pytest.mark.parametrize("bad", ["asym", "loop", "multi", "disconnected", "unsorted"])
+def test_invalid_graphs_rejected(bad):
+    g = S.cycle(6)
+    ro, col = g.row_off.copy(), g.col.copy()
+    want = {"asym": "KC_ERR_NOT_SYMMETRIC", "loop": "KC_ERR_SELF_LOOP",
+            "multi": "KC_ERR_MULTI_EDGE", "disconnected": "KC_ERR_DISCONNECTED",
+            "unsorted": "KC_ERR_MULTI_EDGE"}[bad]
+    if bad == "asym":
+        col[0] = 3  # 0 -> 3 without 3 -> 0 (row 0 becomes [3, 5])
+    elif bad == "loop":
+        col[0] = 0
+    elif bad == "multi":
+        col[1] = col[0]
+    elif bad == "unsorted":
+        col[0], col[1] = col[1], col[0]
+    elif bad == "disconnected":
+        g2 = S.csr_from_edges(6, [0, 1, 3, 4], [1, 2, 4, 5])
+        ro, col = g2.row_off, g2.col
+    st, h = kc.kc_graph_create(ro, col, check=False)
+    assert kc.STATUS[st] == want
+    assert not h
+
+
+def test_step_cap_reports_error_and_keeps_handle():
+    g = S.grid(30, 30)
+    with kc.KemenyGraph.from_graph(g, _cfg(step_cap=100)) as G:
+        st = kc.kc_sample(G.h, 1, 8, check=False)
+        assert kc.STATUS[st] == "KC_ERR_STEP_LIMIT"
+        assert G.stats()["pool_trees"] == 0
+
+
+def test_seed_is_fixed_per_handle():
+    g = S.cycle(10)
+    with kc.KemenyGraph.from_graph(g) as G:
+        G.sample(5, 4)
+        assert kc.STATUS[kc.kc_sample(G.h, 6, 4, check=False)] == "KC_ERR_INVALID_ARG"
+        G.sample(5, 4)
+        assert np.array_equal(G.samples()["sid"], np.arange(8))
+
+
+@pytest.mark.skipif(os.environ.get("KC_SKIP_LARGE") == "1", reason="large workload disabled")
+def test_grid1000_sampled_ids_bit_exact():
+    """Road-shaped full-size workload (1000x1000 grid, 25% edges deleted): the
+    trees the benchmark draws, checked on sampled ids against the oracle."""
+    g = S.workload("grid1000")
+    t0 = O.tau0(g)
+    with kc.KemenyGraph.from_graph(g, _cfg(keep_trees=0)) as G:
+        tau = G.tau0()
+        assert tau["ecc"] == t0.ecc and np.array_equal(tau["in0"], t0.in0)
+        assert G.stats()["ttf_variant"] == kc.KC_TTF_BIT
+        G.sample(1, 64)
+        got = G.samples()
+        ids = [0, 1, 17, 63]
+        for k in ids:
+            ref_f, ref_st = O.sample_batch(g, t0, 1, k, 1)
+            assert got["f"][k] == ref_f[0] and got["steps"][k] == ref_st[0]
+        tr = G.tree(17)
+        ref = O.tree(g, t0, 1, 17)
+        assert np.array_equal(tr["parent"], ref.parent)
+        assert np.array_equal(tr["din"], ref.din)
+        assert np.array_equal(tr["vol"], ref.vol)
