@@ -1,0 +1,379 @@
+"""Benchmark of the TTF Kemeny-constant hot path on GB300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload grid1000] [--trees T]
+    python bench.py --impl reference ...   # the CPU oracle on the host cores
+
+A step is one pass of the sampling hot path over one batch of T trees: Wilson
+walks, per-tree traversal (size, volume, DFN), f(tau) and the pool reduction
+(kc_sample).  Metric: spanning trees per second, whole job (all ranks).  Multi-GPU
+runs shard sample ids across ranks (weak scaling, no collective on the data
+path); the time is the maximum over ranks.  Prints one JSON line on rank 0.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+L2_BYTES = 129 * 1024 * 1024
+SECTOR = 32
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d.get("hbm_gbs", 6800.0)), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.rows = []
+        self.proc = None
+        self.t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.t = threading.Thread(target=self._read, daemon=True)
+        self.t.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+        if self.t is not None:
+            self.t.join(timeout=2)
+        sm = [float(r[1]) for r in self.rows if len(r) >= 9 and r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if len(r) >= 9 and r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in self.rows:
+            if len(r) < 9:
+                continue
+            for k, nm in enumerate(names):
+                if r[5 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(self.rows)}
+
+
+def algorithmic_bytes(phase: str, n: int, ecc: int, trees: int, steps: int) -> float:
+    """Bytes the method must move per launch batch (32-byte sectors):
+    wilson   2 sectors per departure (vertex record; walker word of u, whose line
+             also answers the in-tree test of the next vertex) + 3 per committed vertex;
+    traverse 6 sectors per vertex (three passes, two gathers each);
+    ttf_bit  (3 log2 n + 4) sectors per vertex (query, add, undo chains);
+    ttf_scan 2 ecc sectors per vertex (tau0 ancestor walk)."""
+    lg = math.log2(max(n, 2))
+    if phase == "wilson":
+        return SECTOR * (2.0 * steps + 3.0 * n * trees)
+    if phase == "traverse":
+        return SECTOR * 6.0 * n * trees
+    if phase == "ttf_bit":
+        return SECTOR * (3.0 * lg + 4.0) * n * trees
+    if phase == "ttf_scan":
+        return SECTOR * 2.0 * ecc * n * trees
+    return 0.0
+
+
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch
+        import torch.distributed as dist
+
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        dist.init_process_group(backend=backend)
+        return dist, rank, ws, local
+    return None, rank, ws, local
+
+
+def reduce_max(dist, x: float) -> float:
+    if dist is None:
+        return x
+    import torch
+
+    dev = "cuda" if torch.cuda.is_available() and dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(dist):
+    if dist is not None:
+        dist.barrier()
+
+
+def oracle_baseline(g, trees: int, seed: int, threads: int = 0):
+    """The CPU oracle as it stands: Wilson + traversal + Algorithm 1 over a
+    bounded sample of sample ids, OpenMP across trees on the host cores."""
+    import oracle as O
+
+    t0 = O.tau0(g)
+    t = time.perf_counter()
+    f, steps = O.sample_batch(g, t0, seed, 0, trees, threads=threads)
+    el = time.perf_counter() - t
+    return trees / el, el, O.num_threads() if threads <= 0 else threads
+
+
+def run_reference(args):
+    """--impl reference: the oracle timed on the host cores, same metric/config."""
+    dist, rank, ws, _ = dist_setup()
+    if rank != 0:
+        return
+    from paper_2511_16356_gb300 import synth as S
+
+    g = S.workload(args.workload)
+    per_step = args.ref_trees
+    for _ in range(args.warmup):
+        oracle_baseline(g, per_step, args.seed)
+    times = []
+    cores = 1
+    for _ in range(args.steps):
+        _, el, cores = oracle_baseline(g, per_step, args.seed)
+        times.append(el)
+    tot = sum(times)
+    value = per_step * args.steps / tot
+    line = {
+        "impl": "reference",
+        "metric": "trees/sec", "value": value, "unit": "trees/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * tot / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+        "data": "synthetic",
+        "config": {"workload": S.WORKLOADS.get(args.workload, args.workload),
+                   "trees_per_step": per_step},
+        "cpu_baseline": {"value": value, "unit": "trees/s", "cores": cores, "kind": "oracle",
+                         "sample": f"{per_step} trees (sample ids 0..{per_step - 1}) per step "
+                                   f"of {args.workload}, OpenMP across trees"},
+        "e2e": {"value": value, "unit": "trees/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--workload", default="grid1000")
+    ap.add_argument("--trees", type=int, default=10000)
+    ap.add_argument("--warmup-trees", type=int, default=16,
+                    help="trees per warm-up step (0: same as --trees)")
+    ap.add_argument("--seed", type=int, default=1)
+    ap.add_argument("--eps", type=float, default=0.01)
+    ap.add_argument("--delta", type=float, default=0.05)
+    ap.add_argument("--ref-trees", type=int, default=32)
+    ap.add_argument("--step-cap-per-n", type=int, default=256,
+                    help="Wilson departures allowed per tree, in units of n")
+    ap.add_argument("--walker", default="auto", choices=["auto", "warp", "lane"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-tte", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+    if args.impl == "reference":
+        run_reference(args)
+        return
+
+    import torch
+
+    from paper_2511_16356_gb300 import kc
+    from paper_2511_16356_gb300 import synth as S
+
+    dist, rank, ws, local = dist_setup()
+    torch.cuda.set_device(local)
+    stream = torch.cuda.current_stream()
+    kc.load()
+    g = S.workload(args.workload)
+    n = g.n
+    T = args.trees
+    WT = args.warmup_trees or T
+    ids_per_rank = 1 << 28
+    cfg = kc.kc_config_default()
+    cfg.keep_trees = 0
+    cfg.sample_id_base = rank * ids_per_rank
+    cfg.step_cap = args.step_cap_per_n * n
+    cfg.walker = {"auto": kc.KC_WALK_AUTO, "warp": kc.KC_WALK_WARP,
+                  "lane": kc.KC_WALK_LANE}[args.walker]
+    G = kc.KemenyGraph.from_graph(g, cfg, stream=stream.cuda_stream)
+    st0 = G.stats()
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.int32, device="cuda")
+
+    for _ in range(args.warmup):
+        G.sample(args.seed, WT)
+    torch.cuda.synchronize()
+    kc.kc_reset_timers(G.h)
+    pool0 = G.stats()["pool_trees"]
+    clocks = ClockSampler(local)
+    barrier(dist)
+    torch.cuda.synchronize()
+    clocks.start()
+    step_ms = []
+    for _ in range(args.steps):
+        flush.fill_(1)  # evict L2 between timed steps
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        G.sample(args.seed, T)
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    barrier(dist)
+    tot_ms = reduce_max(dist, float(sum(step_ms)))
+    ms_per_step = tot_ms / args.steps
+    value = T * ws * args.steps / (tot_ms / 1000.0)
+    st = G.stats()
+    samples = G.samples(pool0, st["pool_trees"] - pool0)
+    steps_total = int(samples["steps"].sum())
+    trees_timed = T * args.steps
+
+    # dominant phase, roofline from its CUDA-event time inside kc_sample
+    phases = {
+        "wilson": (st["ms_wilson"], st["launches_wilson"]),
+        "traverse": (st["ms_traverse"], st["launches_traverse"]),
+        "ttf_bit" if st["ttf_variant"] == kc.KC_TTF_BIT else "ttf_scan":
+            (st["ms_ttf"], st["launches_ttf"]),
+    }
+    dom = max(phases, key=lambda k: phases[k][0])
+    dom_ms, dom_launches = phases[dom]
+    alg = algorithmic_bytes(dom, n, st["ecc"], trees_timed, steps_total)
+    peak, peak_kind = _peaks()
+    per_launch_bytes = alg / max(1, dom_launches)
+    per_launch_s = dom_ms / 1000.0 / max(1, dom_launches)
+    achieved = per_launch_bytes / per_launch_s / 1e9
+    launches = sum(st[k] for k in st if k.startswith("launches_") and k != "launches_setup")
+    kernel_name = {"wilson": "k_wilson", "traverse": "k_bottom_up/k_sibling_offsets/k_top_down",
+                   "ttf_bit": "k_ttf_bit", "ttf_scan": "k_ttf_scan"}[dom]
+    phase_ms = {k: round(v[0], 3) for k, v in phases.items()}
+    phase_ms["wave_init"] = round(st["ms_wave_init"], 3)
+    phase_ms["reduce"] = round(st["ms_reduce"], 3)
+
+    out = {
+        "metric": "trees/sec", "value": value, "unit": "trees/s", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+        "data": "synthetic",
+        "config": {"workload": S.WORKLOADS.get(args.workload, args.workload),
+                   "n": n, "m": g.m, "ecc": st["ecc"], "trees_per_step": T,
+                   "trees_per_rank_per_step": T, "parallelism": f"sample-sharded x{ws}",
+                   "l2": "flushed between timed steps (258 MB write); per-step working set "
+                         f"{st['workspace_bytes'] / 1e9:.1f} GB",
+                   "ttf": "BIT" if st["ttf_variant"] == kc.KC_TTF_BIT else "SCAN",
+                   "walker": "lane" if st["walker"] == kc.KC_WALK_LANE else "warp",
+                   "trees_in_flight": st["trees_in_flight"]},
+        "roofline": {"bound": "hbm", "kernel": kernel_name, "achieved": achieved, "peak": peak,
+                     "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": None,
+                     "algorithmic_bytes_per_launch": per_launch_bytes,
+                     "mean_launch_ms": per_launch_s * 1000.0},
+        "phase_ms": phase_ms,
+        "steps_per_tree": steps_total / trees_timed,
+        "gpu_launches": int(launches),
+        "clocks": clk,
+    }
+
+    G.close()  # release its workspace before the other measurements
+
+    # ---- time to eps on a fresh handle (tau0 precomputed, inputs resident)
+    if not args.no_tte and rank == 0:
+        cfg2 = kc.kc_config_default()
+        cfg2.keep_trees = 0
+        cfg2.step_cap = cfg.step_cap
+        cfg2.walker = cfg.walker
+        cfg2.batch_trees = 1024
+        H = kc.KemenyGraph.from_graph(g, cfg2, stream=stream.cuda_stream)
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        k_hat = H.estimate(args.eps, args.delta)
+        tte = time.perf_counter() - t
+        out["time_to_eps"] = {"value": tte, "unit": "s", "eps": args.eps, "delta": args.delta,
+                              "trees": H.stats()["pool_trees"], "K": k_hat,
+                              "rule": "CLT: z s/sqrt(w) <= eps K (1-eps)"}
+        H.close()
+
+    # ---- end to end through the C ABI with host buffers
+    if not args.no_e2e:
+        ro = torch.from_numpy(g.row_off).pin_memory().numpy()
+        co = torch.from_numpy(g.col).pin_memory().numpy()
+        fbuf = torch.empty(T, dtype=torch.int64).pin_memory().numpy()
+
+        def e2e_step():
+            st_, h = kc.kc_graph_create(ro, co, cfg)
+            kc.kc_graph_set_stream(h, stream.cuda_stream)
+            kc.kc_sample(h, args.seed, T)
+            kc.load().kc_get_samples(h, 0, T, fbuf.ctypes.data, None, None, None)
+            kc.kc_graph_destroy(h)
+
+        e2e_step()
+        torch.cuda.synchronize()
+        barrier(dist)
+        k_e2e = max(1, min(args.steps, 2))
+        t = time.perf_counter()
+        for _ in range(k_e2e):
+            e2e_step()
+        torch.cuda.synchronize()
+        el = reduce_max(dist, time.perf_counter() - t)
+        out["e2e"] = {"value": T * ws * k_e2e / el, "unit": "trees/s",
+                      "h2d_bytes_per_step": int(ro.nbytes + co.nbytes),
+                      "d2h_bytes_per_step": int(fbuf.nbytes),
+                      "steps": k_e2e,
+                      "includes": "kc_graph_create from pinned host CSR (validation, "
+                                  "records, BFS tau0, DFN), kc_sample, f read back, destroy"}
+
+    # ---- the CPU oracle on the host cores (rank 0, N = 1 only)
+    if not args.no_cpu_baseline and rank == 0 and ws == 1:
+        cores = os.cpu_count() or 1
+        trees = max(2 * cores, 16)
+        v, el, used = oracle_baseline(g, trees, args.seed)
+        out["cpu_baseline"] = {"value": v, "unit": "trees/s", "cores": used, "kind": "oracle",
+                               "sample": f"{trees} trees (sample ids 0..{trees - 1}) of "
+                                         f"{args.workload}, {el:.1f} s, OpenMP across trees"}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

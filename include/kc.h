@@ -82,6 +82,11 @@ enum { KC_STOP_CLT = 0,        /* z_{1-delta/2} s / sqrt(w) <= eps K_hat (1 - ep
 enum { KC_UPDATE_BSM = 0,      /* Algorithm 2 */
        KC_UPDATE_ISM = 1 };    /* Algorithm 3 */
 
+/* Wilson walkers per tree.  Both give identical trees and step counts. */
+enum { KC_WALK_AUTO = 0,       /* WARP when ecc(r) <= 2 log2 n, else LANE                */
+       KC_WALK_LANE = 1,       /* one sequential walker per tree (one lane)              */
+       KC_WALK_WARP = 2 };     /* 32 concurrent walkers per tree popping cycles in any order */
+
 /* Effective resistance source for insertions (Algorithm 2/3 "Compute R(u,v)"). */
 enum { KC_R_CG = 0,            /* FP64 conjugate gradients on the Laplacian, on the device */
        KC_R_GIVEN = 1 };       /* kc_edge_op.r supplies R(u,v) in G + (u,v)               */
@@ -98,11 +103,15 @@ typedef struct {
                                    untouched trees (the paper's Theorem on BSM)     */
     int32_t inputs_on_device;   /* 1: kc_graph_create arrays are device pointers      */
     int32_t r_source;           /* KC_R_*                                            */
+    int32_t walker;             /* KC_WALK_*: walkers per tree                        */
+    int32_t reserved0;
     int64_t max_trees_in_flight; /* 0: chosen from free device memory               */
     int64_t batch_trees;        /* kc_estimate batch size (0: 1024)                 */
     int64_t max_trees;          /* kc_estimate cap on the pool size (0: 1 << 24)     */
     int64_t step_cap;           /* per-tree cap on Wilson steps (0: max(2^22, 1024 n)) */
     double mem_fraction;        /* share of free device memory for workspaces (0: 0.6) */
+    int64_t sample_id_base;     /* first sample id of the pool (0); ranks of a
+                                   multi-GPU run use disjoint bases, ids < 2^32   */
 } kc_config;
 
 /* Fill *cfg with the defaults listed above. */
@@ -203,7 +212,7 @@ typedef struct {
     int64_t n, m;
     int32_t root, ecc;
     int32_t ttf_variant;         /* resolved KC_TTF_SCAN or KC_TTF_BIT */
-    int32_t pad;
+    int32_t walker;              /* resolved KC_WALK_LANE or KC_WALK_WARP */
     int64_t pool_trees;          /* trees in the pool                        */
     int64_t next_sample_id;      /* never-reused sample id counter           */
     int64_t total_steps;         /* sum of Wilson departures over all samples */
@@ -213,9 +222,9 @@ typedef struct {
     int64_t updates_applied;
     int64_t trees_resampled;     /* trees replaced or transformed by updates  */
     /* device time (ms, CUDA events on the handle's stream) and launches, per phase */
-    double ms_wilson, ms_traverse, ms_ttf, ms_reduce, ms_update, ms_setup;
+    double ms_wilson, ms_traverse, ms_ttf, ms_reduce, ms_update, ms_setup, ms_wave_init;
     int64_t launches_wilson, launches_traverse, launches_ttf, launches_reduce,
-            launches_update, launches_setup;
+            launches_update, launches_setup, launches_wave_init;
     /* sums over the pool: exact sum of w=1 f as two int64 limbs, and FP64 moments */
     int64_t f_sum_hi;            /* high limb (signed) of the int128 sum of f */
     uint64_t f_sum_lo;           /* low limb of the int128 sum of f           */

@@ -106,10 +106,7 @@ size_t ws_size(const kc_graph *g, const Plan &p) {
     b += align256(sizeof(int64_t) * n * p.BT);       // vol
     b += align256(sizeof(int32_t) * n * p.BT);       // din
     b += align256(sizeof(int32_t) * n * p.BT);       // aux
-    if (p.bit) {
-        b += align256(sizeof(int64_t) * (n + 1) * p.BT);       // bit
-        b += align256(sizeof(int32_t) * 4 * (size_t)p.stack_cap * p.BT);  // stack
-    }
+    if (p.bit) b += align256(sizeof(int64_t) * (n + 1) * p.BT);  // bit
     return b;
 }
 
@@ -145,7 +142,7 @@ Carved carve(kc_graph *g, const Plan &p) {
     w.stack_cap = p.stack_cap;
     if (p.bit) {
         w.bit = (int64_t *)take(sizeof(int64_t) * (n + 1) * p.BT);
-        w.stack = (int32_t *)take(sizeof(int32_t) * 4 * (size_t)p.stack_cap * p.BT);
+        w.stack = g->d_stack;  // separate allocation, grown to BT x stack_cap entries
     }
     w.err = g->d_err;
     w.maxdepth = (int32_t *)(g->d_err + 1);
@@ -228,10 +225,18 @@ void run_wave(kc_graph *g, Plan &p, int64_t B, int64_t sid0) {
     KC_CK(g, cudaMemsetAsync(g->d_err, 0, 2 * sizeof(uint32_t), g->stream));
     KC_CK(g, launch_iota(c.sids, sid0, B, g->stream));
     {
-        Phase ph(g, g->t_wilson);
+        Phase ph(g, g->t_init);
         KC_CK(g, launch_wave_init(gv, w, g->stream));
-        KC_CK(g, launch_wilson(gv, w, g->seed, c.sids, step_cap_of(g), g->stream));
-        ph.done(2);
+        ph.done(1);
+    }
+    {
+        Phase ph(g, g->t_wilson);
+        if (g->walker == KC_WALK_LANE)
+            KC_CK(g, launch_wilson(gv, w, g->seed, c.sids, step_cap_of(g), g->stream));
+        else
+            KC_CK(g, launch_wilson_warp(gv, w, g->seed, c.sids, g->d_sorder, step_cap_of(g),
+                                        g->stream));
+        ph.done(1);
     }
     uint32_t hdr[2] = {0, 0};
     KC_CK(g, cudaMemcpy(hdr, g->d_err, sizeof(hdr), cudaMemcpyDeviceToHost));
@@ -239,32 +244,24 @@ void run_wave(kc_graph *g, Plan &p, int64_t B, int64_t sid0) {
         g->last_error = "Wilson walk exceeded the step cap";
         throw Fail{KC_ERR_STEP_LIMIT};
     }
+    if (hdr[0] & (kErrBadTree | kErrIterLimit)) {
+        g->last_error = "Wilson walkers reached an inconsistent state or the iteration cap";
+        throw Fail{KC_ERR_CUDA};
+    }
     if (p.bit) {
+        // DFS stack: one entry per stacked ancestor, so depth + 2 entries suffice
         const int64_t need_cap = (int64_t)hdr[1] + 2;
-        if (need_cap > p.stack_cap) {
-            // re-carve with a larger stack; the Wilson results live in the
-            // leading regions, which keep their offsets only if the layout is
-            // unchanged, so grow into a fresh buffer and copy them across.
-            Plan q = p;
-            q.stack_cap = std::max<int64_t>(need_cap, p.stack_cap * 2);
-            const size_t need = ws_size(g, q);
-            if (need > g->ws_bytes) {
-                void *nb = nullptr;
-                KC_CK(g, cudaMalloc(&nb, need));
-                const size_t keep = align256(sizeof(uint64_t) * g->n * p.BW) +
-                                    align256(sizeof(int32_t) * g->n * p.BW) +
-                                    3 * align256(sizeof(int64_t) * p.BW);
-                KC_CK(g, cudaMemcpyAsync(nb, g->d_ws, keep, cudaMemcpyDeviceToDevice, g->stream));
-                KC_CK(g, cudaStreamSynchronize(g->stream));
-                dfree(g->d_ws);
-                g->d_ws = nb;
-                g->ws_bytes = need;
-            }
-            p = q;
-            c = carve(g, p);
-            w = c.wv;
-            w.B = B;
+        const size_t need = sizeof(int32_t) * 4 * (size_t)need_cap * (size_t)p.BT;
+        if (need > g->stack_bytes) {
+            dfree(g->d_stack);
+            g->stack_bytes = 0;
+            KC_CK(g, cudaMalloc((void **)&g->d_stack, need));
+            g->stack_bytes = need;
         }
+        p.stack_cap = need_cap;
+        c = carve(g, p);
+        w = c.wv;
+        w.B = B;
     }
     for (int64_t sub = 0; sub < B; sub += p.BT) {
         const int64_t b = std::min<int64_t>(p.BT, B - sub);
@@ -417,6 +414,8 @@ kc_status kc_graph_destroy(kc_graph *g) {
     dfree(g->d_sid);
     dfree(g->d_parents);
     dfree(g->d_ws);
+    dfree(g->d_stack);
+    dfree(g->d_sorder);
     dfree(g->d_err);
     if (g->d_scratch) cudaFree(g->d_scratch);
     if (g->ev0) cudaEventDestroy(g->ev0);
@@ -456,6 +455,9 @@ kc_status kc_graph_create(int64_t n, const int64_t *row_off, const int32_t *col,
         KC_CK(g, cudaEventCreate(&g->ev0));
         KC_CK(g, cudaEventCreate(&g->ev1));
         g->n = n;
+        if (cfg.sample_id_base < 0 || cfg.sample_id_base >= ((int64_t)1 << 32))
+            throw Fail{KC_ERR_INVALID_ARG};
+        g->next_sid = cfg.sample_id_base;
         // host copy of the CSR (validated layout, kept for updates)
         g->h_row_off.resize((size_t)n + 1);
         const cudaMemcpyKind kind = cfg.inputs_on_device ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost;
@@ -545,6 +547,32 @@ kc_status kc_graph_create(int64_t n, const int64_t *row_off, const int32_t *col,
                                  g->stream));
         KC_CK(g, cudaStreamSynchronize(g->stream));
         if (unreached) throw Fail{KC_ERR_DISCONNECTED};
+        // Start order of the concurrent walkers: a fixed pseudo-random
+        // permutation (vertices sorted by a 32-bit mix of their id), so that the
+        // 32 walkers of a tree start far apart and rarely block each other.  Any
+        // order gives the same trees; starting walkers next to each other (for
+        // example in BFS order around the root) makes them collide constantly.
+        {
+            std::vector<uint64_t> key((size_t)n);
+            for (int64_t v = 0; v < n; ++v) {
+                uint32_t h = (uint32_t)v * 0x9E3779B1u;
+                h ^= h >> 15;
+                h *= 0x85EBCA77u;
+                h ^= h >> 13;
+                h *= 0xC2B2AE3Du;
+                h ^= h >> 16;
+                key[(size_t)v] = ((uint64_t)h << 32) | (uint64_t)(uint32_t)v;
+            }
+            std::vector<int32_t> order((size_t)n);
+            for (int64_t v = 0; v < n; ++v) order[(size_t)v] = (int32_t)v;
+            std::sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
+                return key[(size_t)a] < key[(size_t)b] || (key[(size_t)a] == key[(size_t)b] && a < b);
+            });
+            dalloc(g, &g->d_sorder, n);
+            KC_CK(g, cudaMemcpyAsync(g->d_sorder, order.data(), sizeof(int32_t) * n,
+                                     cudaMemcpyHostToDevice, g->stream));
+            KC_CK(g, cudaStreamSynchronize(g->stream));
+        }
         // overflow margin: |f| <= 4 m^2 ecc (Theorem 5's proof) must stay below 2^62
         {
             const long double bound = 4.0L * (long double)g->m * (long double)g->m * (long double)g->ecc;
@@ -576,6 +604,12 @@ kc_status kc_graph_create(int64_t n, const int64_t *row_off, const int32_t *col,
         if (variant == KC_TTF_AUTO) variant = (g->ecc <= 2 * lg) ? KC_TTF_SCAN : KC_TTF_BIT;
         if (variant == KC_TTF_BIT && twom >= ((int64_t)1 << 31)) variant = KC_TTF_SCAN;
         g->ttf_variant = variant;
+        // Walkers: 32 per tree pay off when walks are short (low eccentricity);
+        // on long-diameter graphs the concurrent walkers mostly wait on each
+        // other and one walker per tree keeps more trees' walks in flight.
+        int walker = cfg.walker;
+        if (walker == KC_WALK_AUTO) walker = (g->ecc <= 2 * lg) ? KC_WALK_WARP : KC_WALK_LANE;
+        g->walker = walker;
     } catch (Fail &f) {
         kc_graph_destroy(g);
         return f.st;
@@ -597,6 +631,10 @@ kc_status kc_sample(kc_graph *g, uint64_t seed, int64_t n_trees) {
         return KC_ERR_INVALID_ARG;
     }
     if (n_trees == 0) return KC_OK;
+    if (g->next_sid + n_trees > ((int64_t)1 << 32)) {
+        g->last_error = "kc_sample: sample ids must stay below 2^32";
+        return KC_ERR_INVALID_ARG;
+    }
     const bool was_seeded = g->seeded;
     g->seed = seed;
     g->seeded = true;
@@ -741,12 +779,13 @@ kc_status kc_stats(kc_graph *g, kc_stats_t *out) {
     out->root = g->root;
     out->ecc = g->ecc;
     out->ttf_variant = g->ttf_variant;
+    out->walker = g->walker;
     out->pool_trees = g->pool;
     out->next_sample_id = g->next_sid;
     out->trees_in_flight = g->last_wave;
     out->pool_bytes = g->pool_cap * (int64_t)(8 + 8 + 8 + 8) +
                       (g->cfg.keep_trees ? g->pool_cap * g->n * 4 : 0);
-    out->workspace_bytes = (int64_t)g->ws_bytes;
+    out->workspace_bytes = (int64_t)(g->ws_bytes + g->stack_bytes);
     out->updates_applied = g->updates_applied;
     out->trees_resampled = g->trees_resampled;
     out->ms_wilson = g->t_wilson.ms;
@@ -755,6 +794,8 @@ kc_status kc_stats(kc_graph *g, kc_stats_t *out) {
     out->ms_reduce = g->t_reduce.ms;
     out->ms_update = g->t_update.ms;
     out->ms_setup = g->t_setup.ms;
+    out->ms_wave_init = g->t_init.ms;
+    out->launches_wave_init = g->t_init.launches;
     out->launches_wilson = g->t_wilson.launches;
     out->launches_traverse = g->t_traverse.launches;
     out->launches_ttf = g->t_ttf.launches;
@@ -786,7 +827,8 @@ kc_status kc_stats(kc_graph *g, kc_stats_t *out) {
 
 kc_status kc_reset_timers(kc_graph *g) {
     if (!g) return KC_ERR_INVALID_ARG;
-    g->t_wilson = g->t_traverse = g->t_ttf = g->t_reduce = g->t_update = g->t_setup = PhaseTimer();
+    g->t_wilson = g->t_traverse = g->t_ttf = g->t_reduce = g->t_update = g->t_setup =
+        g->t_init = PhaseTimer();
     return KC_OK;
 }
 

@@ -164,6 +164,7 @@ struct kc_graph {
     int32_t root = -1, ecc = 0;
     int32_t *d_p0 = nullptr, *d_level0 = nullptr, *d_in0 = nullptr, *d_out0 = nullptr;
     int32_t ttf_variant = KC_TTF_SCAN;
+    int32_t walker = KC_WALK_WARP;
     // host copy of the graph (validated CSR, needed by updates)
     std::vector<int64_t> h_row_off;
     std::vector<int32_t> h_col;
@@ -181,6 +182,9 @@ struct kc_graph {
     // workspace
     void *d_ws = nullptr;
     size_t ws_bytes = 0;
+    int32_t *d_stack = nullptr;     // BIT-variant DFS stacks, [trees][cap] x int4
+    size_t stack_bytes = 0;
+    int32_t *d_sorder = nullptr;    // start order of the concurrent walkers
     int64_t ws_trees = 0;
     uint32_t *d_err = nullptr;
     void *d_scratch = nullptr;      // small reduction scratch
@@ -189,7 +193,7 @@ struct kc_graph {
     int64_t total_steps = 0;
     int64_t updates_applied = 0, trees_resampled = 0;
     int64_t update_seq = 0;
-    kc::PhaseTimer t_wilson, t_traverse, t_ttf, t_reduce, t_update, t_setup;
+    kc::PhaseTimer t_wilson, t_traverse, t_ttf, t_reduce, t_update, t_setup, t_init;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     std::string last_error;
 };
@@ -213,6 +217,8 @@ cudaError_t launch_level_order(int64_t n, int32_t ecc, const int32_t *level, int
 cudaError_t launch_wave_init(const GraphView &g, WaveView w, cudaStream_t s);
 cudaError_t launch_wilson(const GraphView &g, WaveView w, uint64_t seed, const int64_t *sids,
                           int64_t step_cap, cudaStream_t s);
+cudaError_t launch_wilson_warp(const GraphView &g, WaveView w, uint64_t seed, const int64_t *sids,
+                               const int32_t *sorder, int64_t step_cap, cudaStream_t s);
 cudaError_t launch_traverse(const GraphView &g, WaveView w, bool want_preorder, cudaStream_t s,
                             int *launches);
 cudaError_t launch_ttf_scan(const GraphView &g, WaveView w, cudaStream_t s);

@@ -26,6 +26,7 @@ KC_TTF_AUTO, KC_TTF_SCAN, KC_TTF_BIT = 0, 1, 2
 KC_STOP_CLT, KC_STOP_HOEFFDING = 0, 1
 KC_UPDATE_BSM, KC_UPDATE_ISM = 0, 1
 KC_R_CG, KC_R_GIVEN = 0, 1
+KC_WALK_AUTO, KC_WALK_LANE, KC_WALK_WARP = 0, 1, 2
 KC_OP_INSERT, KC_OP_DELETE = 0, 1
 
 
@@ -35,9 +36,10 @@ class kc_config(ctypes.Structure):
         ("ttf_variant", ctypes.c_int32), ("keep_trees", ctypes.c_int32),
         ("stop_rule", ctypes.c_int32), ("refresh_after_update", ctypes.c_int32),
         ("inputs_on_device", ctypes.c_int32), ("r_source", ctypes.c_int32),
+        ("walker", ctypes.c_int32), ("reserved0", ctypes.c_int32),
         ("max_trees_in_flight", ctypes.c_int64), ("batch_trees", ctypes.c_int64),
         ("max_trees", ctypes.c_int64), ("step_cap", ctypes.c_int64),
-        ("mem_fraction", ctypes.c_double),
+        ("mem_fraction", ctypes.c_double), ("sample_id_base", ctypes.c_int64),
     ]
 
 
@@ -48,7 +50,7 @@ class kc_edge_op(ctypes.Structure):
 
 _STATS_FIELDS = [
     ("n", ctypes.c_int64), ("m", ctypes.c_int64), ("root", ctypes.c_int32),
-    ("ecc", ctypes.c_int32), ("ttf_variant", ctypes.c_int32), ("pad", ctypes.c_int32),
+    ("ecc", ctypes.c_int32), ("ttf_variant", ctypes.c_int32), ("walker", ctypes.c_int32),
     ("pool_trees", ctypes.c_int64), ("next_sample_id", ctypes.c_int64),
     ("total_steps", ctypes.c_int64), ("trees_in_flight", ctypes.c_int64),
     ("pool_bytes", ctypes.c_int64), ("workspace_bytes", ctypes.c_int64),
@@ -56,9 +58,11 @@ _STATS_FIELDS = [
     ("ms_wilson", ctypes.c_double), ("ms_traverse", ctypes.c_double),
     ("ms_ttf", ctypes.c_double), ("ms_reduce", ctypes.c_double),
     ("ms_update", ctypes.c_double), ("ms_setup", ctypes.c_double),
+    ("ms_wave_init", ctypes.c_double),
     ("launches_wilson", ctypes.c_int64), ("launches_traverse", ctypes.c_int64),
     ("launches_ttf", ctypes.c_int64), ("launches_reduce", ctypes.c_int64),
     ("launches_update", ctypes.c_int64), ("launches_setup", ctypes.c_int64),
+    ("launches_wave_init", ctypes.c_int64),
     ("f_sum_hi", ctypes.c_int64), ("f_sum_lo", ctypes.c_uint64),
     ("wf_sum", ctypes.c_double), ("w_sum", ctypes.c_double), ("x2_sum", ctypes.c_double),
 ]
@@ -68,7 +72,7 @@ class kc_stats_t(ctypes.Structure):
     _fields_ = _STATS_FIELDS
 
     def as_dict(self) -> dict:
-        return {k: getattr(self, k) for k, _ in _STATS_FIELDS if k != "pad"}
+        return {k: getattr(self, k) for k, _ in _STATS_FIELDS}
 
 
 # The C prototypes, in header order.

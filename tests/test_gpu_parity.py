@@ -61,14 +61,15 @@ def test_tau0_matches_oracle(name):
         assert np.array_equal(tau["out0"], t0.out0)
 
 
+@pytest.mark.parametrize("walker", [kc.KC_WALK_LANE, kc.KC_WALK_WARP])
 @pytest.mark.parametrize("variant", [kc.KC_TTF_SCAN, kc.KC_TTF_BIT])
 @pytest.mark.parametrize("name", list(SMALL))
-def test_trees_bit_exact(name, variant):
+def test_trees_bit_exact(name, variant, walker):
     g = SMALL[name]()
     t0 = O.tau0(g)
     seed = 4242
     ntrees = 200
-    with kc.KemenyGraph.from_graph(g, _cfg(variant)) as G:
+    with kc.KemenyGraph.from_graph(g, _cfg(variant, walker=walker)) as G:
         G.sample(seed, ntrees)
         got = G.samples()
         f_ref, st_ref = O.sample_batch(g, t0, seed, 0, ntrees)
@@ -91,12 +92,15 @@ def test_launch_shape_does_not_change_trees():
     and sampling in several calls, give the same pool."""
     g = S.er_lcc(400, 0.015, 11)
     with kc.KemenyGraph.from_graph(g) as A, \
-            kc.KemenyGraph.from_graph(g, _cfg(max_trees_in_flight=1)) as B:
+            kc.KemenyGraph.from_graph(g, _cfg(max_trees_in_flight=1)) as B, \
+            kc.KemenyGraph.from_graph(g, _cfg(walker=kc.KC_WALK_LANE, max_trees_in_flight=7)) as C:
         A.sample(9, 64)
         for _ in range(4):
             B.sample(9, 16)
-        a, b = A.samples(), B.samples()
+        C.sample(9, 64)
+        a, b, c = A.samples(), B.samples(), C.samples()
         assert np.array_equal(a["f"], b["f"]) and np.array_equal(a["steps"], b["steps"])
+        assert np.array_equal(a["f"], c["f"]) and np.array_equal(a["steps"], c["steps"])
 
 
 def test_estimate_equals_exact_integer_mean():
@@ -186,7 +190,7 @@ def test_grid1000_sampled_ids_bit_exact():
     trees the benchmark draws, checked on sampled ids against the oracle."""
     g = S.workload("grid1000")
     t0 = O.tau0(g)
-    with kc.KemenyGraph.from_graph(g, _cfg(keep_trees=0)) as G:
+    with kc.KemenyGraph.from_graph(g, _cfg(keep_trees=0, step_cap=256 * g.n)) as G:
         tau = G.tau0()
         assert tau["ecc"] == t0.ecc and np.array_equal(tau["in0"], t0.in0)
         assert G.stats()["ttf_variant"] == kc.KC_TTF_BIT
