@@ -66,7 +66,8 @@ typedef enum {
     KC_ERR_BRIDGE = 12,        /* delete of a bridge (G' would be disconnected)      */
     KC_ERR_NO_SAMPLES = 13,    /* estimate/update needs at least one sampled tree    */
     KC_ERR_NO_DEVICE = 14,     /* no CUDA device, or not an sm_103 device            */
-    KC_ERR_NOT_RETAINED = 15   /* trees were not kept (keep_trees = 0)               */
+    KC_ERR_NOT_RETAINED = 15,  /* trees were not kept (keep_trees = 0)               */
+    KC_ERR_SCRATCH_LIMIT = 16  /* request larger than kc_wilson_noalloc's fixed scratch */
 } kc_status;
 
 /* TTF traversal variant (Theorem 8: O(n min(Delta, log n)) per tree). */
@@ -235,6 +236,42 @@ kc_status kc_stats(kc_graph *g, kc_stats_t *out);
 
 /* Zero the per-phase timers and launch counters of kc_stats. */
 kc_status kc_reset_timers(kc_graph *g);
+
+/*
+ * Wilson sampling without any device allocation.  (The paper has no
+ * counterpart: this is an interface for callers that cannot allocate.)
+ *
+ * Some callers must not call cudaMalloc when they need trees: code running
+ * inside an allocator or memory-pool callback, plugins handed a fixed device
+ * budget by their host application, and latency-critical paths that cannot
+ * afford the driver allocator's unbounded latency and implicit
+ * synchronisation.  This call allocates nothing.  Its only working memory is a
+ * fixed array of 8 Mi walker words (64 MiB) compiled into the library, which
+ * every GPU that loads the library holds until the process exits.
+ *
+ * It draws n_trees uniform spanning trees rooted at `root` with sample ids
+ * first_sample_id .. first_sample_id + n_trees - 1 under `seed`, using the
+ * same random-number contract as kc_sample, so the trees and step counts are
+ * identical to the ones kc_sample / kc_get_tree produce for those ids.
+ *  d_row_off, d_col  device CSR as for kc_graph_create (caller-owned, not checked)
+ *  step_cap          per-tree cap on departures (0: max(2^22, 1024 n))
+ *  d_parent          device int32[n_trees][n] out: parent of each vertex (-1 at root)
+ *  d_steps           device int64[n_trees] out: Wilson departures per tree
+ *  d_status          device uint32[1] out: 0, or 1 if a tree hit step_cap
+ *  stream            cudaStream_t to run on (NULL: legacy default stream)
+ * Work is enqueued on `stream`; the call returns without synchronising.
+ * Requires n * n_trees <= 8 Mi, else KC_ERR_SCRATCH_LIMIT.  The first call on
+ * a device looks up the array's device address (cudaGetSymbolAddress) with
+ * that device current; make that first call before any stream capture.
+ * Every call reuses the same array and clears the part it needs; calls that
+ * overlap on the GPU (several streams or host threads) race on it and must be
+ * serialised by the caller.
+ * Errors: INVALID_ARG, SCRATCH_LIMIT, NO_DEVICE, CUDA.
+ */
+kc_status kc_wilson_noalloc(int64_t n, const int64_t *d_row_off, const int32_t *d_col,
+                            int32_t root, uint64_t seed, int64_t first_sample_id,
+                            int64_t n_trees, int64_t step_cap, int32_t *d_parent,
+                            int64_t *d_steps, uint32_t *d_status, void *stream);
 
 /* Static description of a status code (never NULL). */
 const char *kc_status_string(kc_status s);

@@ -392,6 +392,8 @@ const char *kc_status_string(kc_status s) {
         case KC_ERR_NO_SAMPLES: return "no sampled trees";
         case KC_ERR_NO_DEVICE: return "no sm_103 CUDA device";
         case KC_ERR_NOT_RETAINED: return "trees were not retained (keep_trees = 0)";
+        case KC_ERR_SCRATCH_LIMIT:
+            return "request exceeds the 8 Mi-word (64 MiB) fixed scratch of kc_wilson_noalloc";
     }
     return "unknown status";
 }

@@ -21,6 +21,7 @@ STATUS = {
     7: "KC_ERR_OUT_OF_MEMORY", 8: "KC_ERR_CUDA", 9: "KC_ERR_STEP_LIMIT",
     10: "KC_ERR_EDGE_EXISTS", 11: "KC_ERR_EDGE_MISSING", 12: "KC_ERR_BRIDGE",
     13: "KC_ERR_NO_SAMPLES", 14: "KC_ERR_NO_DEVICE", 15: "KC_ERR_NOT_RETAINED",
+    16: "KC_ERR_SCRATCH_LIMIT",
 }
 KC_TTF_AUTO, KC_TTF_SCAN, KC_TTF_BIT = 0, 1, 2
 KC_STOP_CLT, KC_STOP_HOEFFDING = 0, 1
@@ -90,6 +91,9 @@ _SIGS = {
     "kc_get_tree": (ctypes.c_int, [_P, ctypes.c_int64, _P, _P, _P, _P, _P, _P, _P]),
     "kc_get_samples": (ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_int64, _P, _P, _P, _P]),
     "kc_get_tau0": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P]),
+    "kc_wilson_noalloc": (ctypes.c_int, [ctypes.c_int64, _P, _P, ctypes.c_int32, ctypes.c_uint64,
+                                         ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, _P, _P,
+                                         _P, _P]),
     "kc_stats": (ctypes.c_int, [_P, ctypes.POINTER(kc_stats_t)]),
     "kc_reset_timers": (ctypes.c_int, [_P]),
     "kc_status_string": (ctypes.c_char_p, [ctypes.c_int]),
