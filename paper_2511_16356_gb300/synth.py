@@ -196,9 +196,21 @@ def random_connected(n: int, p: float, seed: int) -> Graph:
 
 def er_lcc(n: int, p: float, seed: int) -> Graph:
     rng = np.random.default_rng(seed)
-    iu = np.triu_indices(n, 1)
-    keep = rng.random(iu[0].shape[0]) < p
-    g = csr_from_edges(n, iu[0][keep], iu[1][keep], f"er{n}_{seed}")
+    if n <= 5000:
+        iu = np.triu_indices(n, 1)
+        keep = rng.random(iu[0].shape[0]) < p
+        g = csr_from_edges(n, iu[0][keep], iu[1][keep], f"er{n}_{seed}")
+        return largest_cc(g)
+    # large n: successes of the pair sequence (i < j, row-major) by geometric gaps
+    npairs = n * (n - 1) // 2
+    want = int(npairs * p + 10 * np.sqrt(npairs * p) + 100)
+    gaps = rng.geometric(p, size=want).astype(np.int64)
+    idx = np.cumsum(gaps) - 1
+    idx = idx[idx < npairs]
+    row_start = np.concatenate([[0], np.cumsum(np.arange(n - 1, 0, -1, dtype=np.int64))])
+    i = np.searchsorted(row_start, idx, side="right") - 1
+    j = i + 1 + (idx - row_start[i])
+    g = csr_from_edges(n, i, j, f"er{n}_{seed}")
     return largest_cc(g)
 
 
@@ -312,4 +324,9 @@ def workload(name: str) -> Graph:
     if name.startswith("grid") and "x" in name:
         w, h = name[4:].split("x")
         return grid_perturbed(int(w), int(h), 0.25, 1)
+    if name.startswith("er") and name[2:].isdigit():
+        n = int(name[2:])
+        return er_lcc(n, 8.0 / (n - 1), 0)
+    if name.startswith("cl") and name[2:].isdigit():
+        return chung_lu(int(name[2:]), 2.1, 17.0, 2)
     raise KeyError(name)
