@@ -14,7 +14,8 @@ import numpy as np
 __all__ = [
     "build_oracle", "lib", "philox4x32_10", "bounded", "root", "bfs_tree", "Tau0",
     "tau0", "wilson", "traverse", "f_naive", "f_alg1", "TreeOut", "tree",
-    "sample_batch", "num_threads", "STEP_CAP_DEFAULT",
+    "sample_batch", "num_threads", "STEP_CAP_DEFAULT", "cond_wilson", "select", "link_cut",
+    "cut_link",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -67,6 +68,15 @@ def lib():
             L.orc_sample_batch.argtypes = [c_i64, vp, vp, c_i32, vp, vp, vp, c_u64, c_u32, c_i64,
                                            ctypes.c_int, ctypes.c_int, c_i64, vp, vp]
             L.orc_sample_batch.restype = ctypes.c_int
+            L.orc_cond_wilson.argtypes = [c_i64, vp, vp, c_i32, c_i32, c_i32, c_u64, c_u32, vp,
+                                          vp, c_i64]
+            L.orc_cond_wilson.restype = ctypes.c_int
+            L.orc_select.argtypes = [c_u64, c_u32, c_i64, c_i64, vp]
+            L.orc_select.restype = None
+            for fn in (L.orc_link_cut, L.orc_cut_link):
+                fn.argtypes = [c_i64, vp, vp, vp, c_i32, c_i32, c_i32, c_u64, c_u32, c_u32, c_i64,
+                               vp, vp, vp]
+                fn.restype = ctypes.c_int
             L.orc_num_threads.argtypes = []
             L.orc_num_threads.restype = ctypes.c_int
             _handle = L
@@ -191,3 +201,39 @@ def sample_batch(g, t0: Tau0, seed: int, id0: int, count: int, method: str = "al
     if rc:
         raise RuntimeError("step cap exceeded")
     return f, steps
+
+
+def cond_wilson(g, u: int, v: int, r: int, seed: int, sample: int, cap: int = STEP_CAP_DEFAULT):
+    """Uniform spanning tree of g conditioned on containing (u, v), rooted at r."""
+    parent = np.empty(g.n, dtype=np.int32)
+    steps = np.zeros(1, dtype=np.int64)
+    rc = lib().orc_cond_wilson(g.n, _p(g.row_off), _p(g.col), u, v, r, seed, sample, _p(parent),
+                               _p(steps), cap)
+    if rc:
+        raise RuntimeError("step cap exceeded")
+    return parent, int(steps[0])
+
+
+def select(seed: int, seq: int, N: int, k: int) -> np.ndarray:
+    out = np.empty(max(k, 1), dtype=np.int64)
+    lib().orc_select(seed, seq, N, k, _p(out))
+    return out[:k]
+
+
+def _transform(fn, g, parent, r, u, v, seed, seq, pool_idx, k_force):
+    out = np.empty(g.n, dtype=np.int32)
+    d_old = np.zeros(1, dtype=np.int64)
+    d_new = np.zeros(1, dtype=np.int64)
+    fn(g.n, _p(g.row_off), _p(g.col), _p(np.ascontiguousarray(parent, dtype=np.int32)), r, u, v,
+       seed, seq, pool_idx, k_force, _p(out), _p(d_old), _p(d_new))
+    return out, int(d_old[0]), int(d_new[0])
+
+
+def link_cut(g, parent, r, u, v, seed=0, seq=0, pool_idx=0, k_force=-1):
+    """link-cut of a tree of g - (u,v) into a tree of g (which contains (u,v))."""
+    return _transform(lib().orc_link_cut, g, parent, r, u, v, seed, seq, pool_idx, k_force)
+
+
+def cut_link(g, parent, r, u, v, seed=0, seq=0, pool_idx=0, k_force=-1):
+    """cut-link of a tree containing (u,v) into a tree of g (from which (u,v) is removed)."""
+    return _transform(lib().orc_cut_link, g, parent, r, u, v, seed, seq, pool_idx, k_force)
