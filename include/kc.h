@@ -186,9 +186,10 @@ kc_status kc_update(kc_graph *g, const kc_edge_op *ops, int64_t n_ops, int32_t m
  * Any output pointer may be NULL.  Arrays have n entries (host memory):
  * parent (parent[r] = -1), depth, DFN in/out (preorder from 0, children in
  * ascending id, out = in + size - 1), vol (subtree volume, int64).  Scalars:
- * f (int64), steps (Wilson departures).  For trees never updated the arrays are
- * recomputed on the device from (seed, sample id); updated trees need
- * keep_trees.  Errors: INVALID_ARG, NOT_RETAINED, OUT_OF_MEMORY, CUDA.
+ * f (int64, as stored in the pool), steps (Wilson departures).  With
+ * keep_trees the arrays come from the retained parent array, traversed on the
+ * current graph; without it they are recomputed on the device from (seed,
+ * sample id).  Errors: INVALID_ARG, NOT_RETAINED, OUT_OF_MEMORY, CUDA.
  */
 kc_status kc_get_tree(kc_graph *g, int64_t sample, int32_t *parent, int32_t *depth,
                       int32_t *dfn_in, int32_t *dfn_out, int64_t *vol, int64_t *f,
@@ -230,6 +231,8 @@ typedef struct {
     int64_t f_sum_hi;            /* high limb (signed) of the int128 sum of f */
     uint64_t f_sum_lo;           /* low limb of the int128 sum of f           */
     double wf_sum, w_sum, x2_sum; /* sum w f/(2m), sum w, sum (f/2m)^2 over the pool */
+    double last_resistance;      /* R(u,v) used by the last insertion            */
+    int64_t last_cg_iters;       /* CG iterations of the last computed R          */
 } kc_stats_t;
 
 kc_status kc_stats(kc_graph *g, kc_stats_t *out);

@@ -39,7 +39,7 @@ __global__ void __launch_bounds__(128) k_wilson(GraphView g, WaveView w, uint64_
     const uint32_t sample = (uint32_t)sids[t];
 
     int64_t steps = 0;
-    int32_t pos = 1;       // ord[0] = root
+    int32_t pos = w.pos0;  // ord[0 .. pos0) already placed (the root, or an edge)
     int32_t s = 0;         // current start vertex
     int32_t u = 0;         // walker position (WALK) / path cursor (COUNT, COMMIT)
     uint64_t wu = 0;       // word of u (WALK)
@@ -214,7 +214,7 @@ __global__ void __launch_bounds__(128) k_wilson_warp(GraphView g, WaveView w, ui
     int32_t len = 0, i = 0, dh = 0, mypos = 0, maxd = 0;
     int64_t steps = 0;
     int64_t next_start = 0;  // warp-uniform
-    int64_t pos = 1;         // warp-uniform, ord[0] = root
+    int64_t pos = w.pos0;    // warp-uniform, ord[0 .. pos0) already placed
     bool bad = false;
 
     for (int64_t it = 0;; ++it) {

@@ -207,6 +207,20 @@ Plan plan_for(kc_graph *g, int64_t ntrees) {
     return p;
 }
 
+// DFS stack of the BIT variant: one entry per stacked ancestor, so the
+// deepest tree's depth + 2 entries per tree suffice.
+void ensure_stack(kc_graph *g, Plan &p, uint32_t maxdepth) {
+    const int64_t need_cap = (int64_t)maxdepth + 2;
+    const size_t need = sizeof(int32_t) * 4 * (size_t)need_cap * (size_t)p.BT;
+    if (need > g->stack_bytes) {
+        dfree(g->d_stack);
+        g->stack_bytes = 0;
+        KC_CK(g, cudaMalloc((void **)&g->d_stack, need));
+        g->stack_bytes = need;
+    }
+    p.stack_cap = need_cap;
+}
+
 // Per-tree cap on Wilson departures: the configured value, or
 // max(2^22, 1024 n) (about 60 times the mean step count of a road-shaped
 // graph, far above that of low-diameter graphs).
@@ -249,16 +263,7 @@ void run_wave(kc_graph *g, Plan &p, int64_t B, int64_t sid0) {
         throw Fail{KC_ERR_CUDA};
     }
     if (p.bit) {
-        // DFS stack: one entry per stacked ancestor, so depth + 2 entries suffice
-        const int64_t need_cap = (int64_t)hdr[1] + 2;
-        const size_t need = sizeof(int32_t) * 4 * (size_t)need_cap * (size_t)p.BT;
-        if (need > g->stack_bytes) {
-            dfree(g->d_stack);
-            g->stack_bytes = 0;
-            KC_CK(g, cudaMalloc((void **)&g->d_stack, need));
-            g->stack_bytes = need;
-        }
-        p.stack_cap = need_cap;
+        ensure_stack(g, p, hdr[1]);
         c = carve(g, p);
         w = c.wv;
         w.B = B;
@@ -289,6 +294,406 @@ void run_wave(kc_graph *g, Plan &p, int64_t B, int64_t sid0) {
         g->last_error = "inconsistent tree state or traversal stack overflow";
         throw Fail{KC_ERR_CUDA};
     }
+}
+
+
+// tau0 = BFS tree from g->root over the current device graph (parent = the
+// smallest-id neighbour one level closer), level-synchronous, one launch per
+// level; sets g->ecc.  Throws KC_ERR_DISCONNECTED if a vertex is unreached.
+void build_tau0(kc_graph *g, int &launches) {
+    GraphView gv = view_of(g);
+    const int64_t n = g->n;
+    KC_CK(g, launch_bfs_init(n, g->root, g->d_level0, g->stream));
+    ++launches;
+    int32_t *d_changed = (int32_t *)g->d_scratch;
+    int32_t lev = 0;
+    for (;; ++lev) {
+        KC_CK(g, cudaMemsetAsync(d_changed, 0, sizeof(int32_t), g->stream));
+        KC_CK(g, launch_bfs_level(gv, lev, g->d_level0, d_changed, g->stream));
+        ++launches;
+        int32_t changed = 0;
+        KC_CK(g, cudaMemcpyAsync(&changed, d_changed, sizeof(changed), cudaMemcpyDeviceToHost,
+                                 g->stream));
+        KC_CK(g, cudaStreamSynchronize(g->stream));
+        if (!changed) break;
+        if (lev > n) throw Fail{KC_ERR_CUDA};
+    }
+    g->ecc = lev;
+    gv.ecc = lev;
+    int32_t *d_unreached = (int32_t *)g->d_scratch;
+    KC_CK(g, cudaMemsetAsync(d_unreached, 0, sizeof(int32_t), g->stream));
+    KC_CK(g, launch_bfs_parent(gv, g->d_level0, g->d_p0, d_unreached, g->stream));
+    ++launches;
+    int32_t unreached = 0;
+    KC_CK(g, cudaMemcpyAsync(&unreached, d_unreached, sizeof(int32_t), cudaMemcpyDeviceToHost,
+                             g->stream));
+    KC_CK(g, cudaStreamSynchronize(g->stream));
+    if (unreached) throw Fail{KC_ERR_DISCONNECTED};
+}
+
+// DFN of tau0 with the same passes as the sampled trees (one tree).
+void traverse_tau0(kc_graph *g, int &launches) {
+    GraphView gv = view_of(g);
+    const int64_t n = g->n;
+    Plan p;
+    p.BW = 1;
+    p.BT = 1;
+    ensure_ws(g, p);
+    Carved c = carve(g, p);
+    WaveView w = c.wv;
+    w.B = 1;
+    KC_CK(g, launch_tau0_words(n, g->d_p0, g->d_level0, w.word, g->stream));
+    KC_CK(g, launch_level_order(n, g->ecc, g->d_level0, w.din, w.ord, g->stream));
+    int nl = 0;
+    KC_CK(g, launch_traverse(gv, w, false, g->stream, &nl));
+    KC_CK(g, launch_out_from_size(n, w.din, w.size, g->d_out0, g->stream));
+    KC_CK(g, cudaMemcpyAsync(g->d_in0, w.din, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice,
+                             g->stream));
+    launches += 4 + nl;
+}
+
+
+// ===========================================================================
+// Sample maintenance (Algorithms 2 and 3)
+// ===========================================================================
+bool has_edge_h(const std::vector<int64_t> &ro, const std::vector<int32_t> &col, int32_t a,
+                int32_t b) {
+    return std::binary_search(col.begin() + ro[(size_t)a], col.begin() + ro[(size_t)a + 1], b);
+}
+
+// insert or erase (u, v) and (v, u) in a CSR kept sorted row by row
+void mutate_csr(std::vector<int64_t> &ro, std::vector<int32_t> &col, int32_t u, int32_t v,
+                bool insert) {
+    const int64_t n = (int64_t)ro.size() - 1;
+    for (int pass = 0; pass < 2; ++pass) {
+        const int32_t a = pass == 0 ? u : v, b = pass == 0 ? v : u;
+        auto first = col.begin() + ro[(size_t)a], last = col.begin() + ro[(size_t)a + 1];
+        auto it = std::lower_bound(first, last, b);
+        if (insert) col.insert(it, b); else col.erase(it);
+        for (int64_t x = a + 1; x <= n; ++x) ro[(size_t)x] += insert ? 1 : -1;
+    }
+}
+
+bool connected_h(const std::vector<int64_t> &ro, const std::vector<int32_t> &col) {
+    const int64_t n = (int64_t)ro.size() - 1;
+    std::vector<uint8_t> seen((size_t)n, 0);
+    std::vector<int32_t> q;
+    q.reserve((size_t)n);
+    q.push_back(0);
+    seen[0] = 1;
+    for (size_t h = 0; h < q.size(); ++h) {
+        const int32_t x = q[h];
+        for (int64_t e = ro[(size_t)x]; e < ro[(size_t)x + 1]; ++e)
+            if (!seen[(size_t)col[(size_t)e]]) {
+                seen[(size_t)col[(size_t)e]] = 1;
+                q.push_back(col[(size_t)e]);
+            }
+    }
+    return (int64_t)q.size() == n;
+}
+
+// The whole batch against the evolving graph, before anything is applied.
+kc_status validate_batch(kc_graph *g, const kc_edge_op *ops, int64_t n_ops) {
+    std::vector<int64_t> ro = g->h_row_off;
+    std::vector<int32_t> col = g->h_col;
+    for (int64_t i = 0; i < n_ops; ++i) {
+        const kc_edge_op &o = ops[i];
+        if (o.u < 0 || o.v < 0 || o.u >= g->n || o.v >= g->n || o.u == o.v ||
+            (o.op != 0 && o.op != 1))
+            return KC_ERR_INVALID_ARG;
+        if (o.op == 0 && g->cfg.r_source == KC_R_GIVEN && !(o.r > 0.0 && o.r <= 1.0))
+            return KC_ERR_INVALID_ARG;
+        const bool present = has_edge_h(ro, col, o.u, o.v);
+        if (o.op == 0 && present) return KC_ERR_EDGE_EXISTS;
+        if (o.op == 1 && !present) return KC_ERR_EDGE_MISSING;
+        mutate_csr(ro, col, o.u, o.v, o.op == 0);
+        if (o.op == 1 && !connected_h(ro, col)) return KC_ERR_BRIDGE;
+    }
+    return KC_OK;
+}
+
+// copy the host CSR to the device and rebuild the walk records and degrees
+void upload_graph(kc_graph *g) {
+    const int64_t n = g->n, twom = g->h_row_off[(size_t)n];
+    if ((size_t)twom > g->col_cap) {
+        dfree(g->d_col);
+        const size_t cap = (size_t)twom + (size_t)twom / 8 + 64;
+        dalloc(g, &g->d_col, cap);
+        g->col_cap = cap;
+    }
+    KC_CK(g, cudaMemcpyAsync(g->d_row_off, g->h_row_off.data(), sizeof(int64_t) * (n + 1),
+                             cudaMemcpyHostToDevice, g->stream));
+    KC_CK(g, cudaMemcpyAsync(g->d_col, g->h_col.data(), sizeof(int32_t) * twom,
+                             cudaMemcpyHostToDevice, g->stream));
+    g->m = twom / 2;
+    KC_CK(g, launch_build_records(view_of(g), g->d_rec, g->d_deg, g->stream));
+    KC_CK(g, cudaStreamSynchronize(g->stream));
+}
+
+struct UpdBuf {
+    int64_t *slots;   // [P]
+    double *factor;   // [P]
+    int64_t *sel;     // [P]
+    uint8_t *flags;   // [P]
+    uint8_t *taken;   // [P]
+    double *sums;     // [4]
+};
+
+UpdBuf upd_buf(kc_graph *g) {
+    const size_t P = (size_t)std::max<int64_t>(g->pool, 1);
+    const size_t need = align256(8 * P) * 3 + align256(P) * 2 + 256;
+    if (need > g->ub_bytes) {
+        if (g->d_ub) cudaFree(g->d_ub);
+        g->d_ub = nullptr;
+        g->ub_bytes = 0;
+        KC_CK(g, cudaMalloc(&g->d_ub, need));
+        g->ub_bytes = need;
+    }
+    char *b = (char *)g->d_ub;
+    UpdBuf u;
+    u.slots = (int64_t *)b;
+    b += align256(8 * P);
+    u.factor = (double *)b;
+    b += align256(8 * P);
+    u.sel = (int64_t *)b;
+    b += align256(8 * P);
+    u.flags = (uint8_t *)b;
+    b += align256(P);
+    u.taken = (uint8_t *)b;
+    b += align256(P);
+    u.sums = (double *)b;
+    return u;
+}
+
+void check_err(kc_graph *g, const char *what) {
+    uint32_t hdr[2] = {0, 0};
+    KC_CK(g, cudaMemcpy(hdr, g->d_err, sizeof(hdr), cudaMemcpyDeviceToHost));
+    if (hdr[0] & kErrStepLimit) {
+        g->last_error = std::string(what) + ": Wilson walk exceeded the step cap";
+        throw Fail{KC_ERR_STEP_LIMIT};
+    }
+    if (hdr[0]) {
+        g->last_error = std::string(what) + ": inconsistent tree state";
+        throw Fail{KC_ERR_CUDA};
+    }
+}
+
+// traversal and f(tau) of the retained trees at `slots`, on the current graph
+void refresh_slots(kc_graph *g, const std::vector<int64_t> &slots) {
+    if (slots.empty()) return;
+    GraphView gv = view_of(g);
+    Plan p = plan_for(g, (int64_t)slots.size());
+    ensure_ws(g, p);
+    UpdBuf ub = upd_buf(g);
+    for (size_t c0 = 0; c0 < slots.size(); c0 += (size_t)p.BT) {
+        const int64_t b = std::min<int64_t>(p.BT, (int64_t)(slots.size() - c0));
+        KC_CK(g, cudaMemcpyAsync(ub.slots, slots.data() + c0, sizeof(int64_t) * b,
+                                 cudaMemcpyHostToDevice, g->stream));
+        KC_CK(g, cudaMemsetAsync(g->d_err, 0, 2 * sizeof(uint32_t), g->stream));
+        Carved c = carve(g, p);
+        WaveView w = c.wv;
+        w.B = b;
+        KC_CK(g, launch_prepare_from_parents(g->n, b, g->root, g->d_parents, ub.slots, w,
+                                             g->stream));
+        uint32_t hdr[2] = {0, 0};
+        KC_CK(g, cudaMemcpyAsync(hdr, g->d_err, sizeof(hdr), cudaMemcpyDeviceToHost, g->stream));
+        KC_CK(g, cudaStreamSynchronize(g->stream));
+        if (hdr[0]) check_err(g, "refresh");
+        if (p.bit) {
+            ensure_stack(g, p, hdr[1]);
+            c = carve(g, p);
+            w = c.wv;
+            w.B = b;
+        }
+        int nl = 0;
+        KC_CK(g, launch_traverse(gv, w, p.bit, g->stream, &nl));
+        if (p.bit) KC_CK(g, launch_ttf_bit(gv, w, g->stream));
+        else KC_CK(g, launch_ttf_scan(gv, w, g->stream));
+        KC_CK(g, launch_scatter_results(ub.slots, b, w.f, nullptr, nullptr, g->d_f, g->d_steps,
+                                        g->d_sid, g->stream));
+        g->t_update.launches += nl + 6;
+        check_err(g, "refresh");
+    }
+}
+
+// replace the retained trees at `slots` by fresh trees with new sample ids
+// (in slot order): uniform trees of the current graph, or, with cond, uniform
+// trees conditioned on containing (u, v), re-rooted at r
+void resample_slots(kc_graph *g, const std::vector<int64_t> &slots, bool cond, int32_t u,
+                    int32_t v) {
+    if (slots.empty()) return;
+    GraphView gv = view_of(g);
+    Plan p = plan_for(g, (int64_t)slots.size());
+    ensure_ws(g, p);
+    UpdBuf ub = upd_buf(g);
+    const int64_t chunk = std::min(p.BW, p.BT);
+    for (size_t c0 = 0; c0 < slots.size(); c0 += (size_t)chunk) {
+        const int64_t b = std::min<int64_t>(chunk, (int64_t)(slots.size() - c0));
+        KC_CK(g, cudaMemcpyAsync(ub.slots, slots.data() + c0, sizeof(int64_t) * b,
+                                 cudaMemcpyHostToDevice, g->stream));
+        KC_CK(g, cudaMemsetAsync(g->d_err, 0, 2 * sizeof(uint32_t), g->stream));
+        Carved c = carve(g, p);
+        WaveView w = c.wv;
+        w.B = b;
+        KC_CK(g, launch_iota(c.sids, g->next_sid, b, g->stream));
+        if (cond) {
+            KC_CK(g, launch_edge_pre_init(g->n, b, u, v, w.word, w.ord, g->stream));
+            w.pos0 = 2;
+        } else {
+            KC_CK(g, launch_wave_init(gv, w, g->stream));
+            w.pos0 = 1;
+        }
+        if (g->walker == KC_WALK_LANE)
+            KC_CK(g, launch_wilson(gv, w, g->seed, c.sids, step_cap_of(g), g->stream));
+        else
+            KC_CK(g, launch_wilson_warp(gv, w, g->seed, c.sids, g->d_sorder, step_cap_of(g),
+                                        g->stream));
+        KC_CK(g, launch_words_to_slots(g->n, b, w.word, ub.slots, g->d_parents, g->root,
+                                       cond ? v : -1, g->d_err, g->stream));
+        KC_CK(g, launch_scatter_results(ub.slots, b, nullptr, w.steps, c.sids, g->d_f,
+                                        g->d_steps, g->d_sid, g->stream));
+        check_err(g, "resample");
+        g->next_sid += b;
+        g->t_update.launches += 5;
+        std::vector<int64_t> part(slots.begin() + c0, slots.begin() + c0 + b);
+        for (int64_t x : part) g->h_modified[(size_t)x] = 1;
+        refresh_slots(g, part);
+    }
+    g->trees_resampled += (int64_t)slots.size();
+}
+
+// ISM: link-cut (insert) or cut-link (delete) of the trees at `slots`, their
+// weights multiplied by d_old / d_new, then their f recomputed
+void transform_slots(kc_graph *g, const std::vector<int64_t> &slots, bool insert, int32_t u,
+                     int32_t v) {
+    if (slots.empty()) return;
+    GraphView gv = view_of(g);
+    Plan p = plan_for(g, (int64_t)slots.size());
+    ensure_ws(g, p);
+    UpdBuf ub = upd_buf(g);
+    for (size_t c0 = 0; c0 < slots.size(); c0 += (size_t)p.BT) {
+        const int64_t b = std::min<int64_t>(p.BT, (int64_t)(slots.size() - c0));
+        KC_CK(g, cudaMemcpyAsync(ub.slots, slots.data() + c0, sizeof(int64_t) * b,
+                                 cudaMemcpyHostToDevice, g->stream));
+        KC_CK(g, cudaMemsetAsync(g->d_err, 0, 2 * sizeof(uint32_t), g->stream));
+        Carved c = carve(g, p);
+        WaveView w = c.wv;
+        w.B = b;
+        KC_CK(g, launch_prepare_from_parents(g->n, b, g->root, g->d_parents, ub.slots, w,
+                                             g->stream));
+        int nl = 0;
+        KC_CK(g, launch_traverse(gv, w, true, g->stream, &nl));
+        KC_CK(g, launch_link_cut(g->d_row_off, g->d_col, w, ub.slots, g->d_parents, ub.factor,
+                                 g->root, u, v, g->seed, (uint32_t)g->update_seq, insert,
+                                 g->stream));
+        KC_CK(g, launch_scale_slots(g->d_w, ub.slots, ub.factor, b, g->stream));
+        check_err(g, insert ? "link-cut" : "cut-link");
+        g->t_update.launches += nl + 7;
+        std::vector<int64_t> part(slots.begin() + c0, slots.begin() + c0 + b);
+        for (int64_t x : part) g->h_modified[(size_t)x] = 1;
+    }
+    refresh_slots(g, slots);
+    g->trees_resampled += (int64_t)slots.size();
+}
+
+std::vector<int64_t> all_slots(kc_graph *g) {
+    std::vector<int64_t> s((size_t)g->pool);
+    for (int64_t i = 0; i < g->pool; ++i) s[(size_t)i] = i;
+    return s;
+}
+
+double weight_sum(kc_graph *g, const std::vector<uint8_t> &flags, int which) {
+    UpdBuf ub = upd_buf(g);
+    KC_CK(g, cudaMemcpyAsync(ub.flags, flags.data(), flags.size(), cudaMemcpyHostToDevice,
+                             g->stream));
+    KC_CK(g, launch_weight_sums(g->d_w, ub.flags, g->pool, ub.sums, g->stream));
+    double s2[2];
+    KC_CK(g, cudaMemcpyAsync(s2, ub.sums, sizeof(s2), cudaMemcpyDeviceToHost, g->stream));
+    KC_CK(g, cudaStreamSynchronize(g->stream));
+    return which == 2 ? s2[0] + s2[1] : s2[which];
+}
+
+void apply_insert(kc_graph *g, int32_t u, int32_t v, int32_t mode, double r_given) {
+    mutate_csr(g->h_row_off, g->h_col, u, v, true);
+    upload_graph(g);
+    double R = r_given;
+    if (g->cfg.r_source != KC_R_GIVEN) {
+        int nl = 0;
+        int64_t iters = 0;
+        KC_CK(g, resistance_cg(view_of(g), u, v, 1e-13, 50 * g->n + 1000, &R, &iters, &nl,
+                               g->stream));
+        g->t_update.launches += nl;
+        g->last_cg_iters = iters;
+    }
+    g->last_r = R;
+    const int64_t N = g->pool;
+    const int64_t k = std::min<int64_t>(N, (int64_t)std::ceil(R * (double)N));
+    UpdBuf ub = upd_buf(g);
+    std::vector<int64_t> sel((size_t)k);
+    if (k > 0) {
+        KC_CK(g, launch_select(g->seed, (uint32_t)g->update_seq, N, k, ub.taken, ub.sel, g->stream));
+        KC_CK(g, cudaMemcpyAsync(sel.data(), ub.sel, sizeof(int64_t) * k, cudaMemcpyDeviceToHost,
+                                 g->stream));
+        KC_CK(g, cudaStreamSynchronize(g->stream));
+        g->t_update.launches += 1;
+    }
+    std::sort(sel.begin(), sel.end());
+    if (mode == KC_UPDATE_BSM) {
+        resample_slots(g, sel, true, u, v);
+    } else {
+        std::vector<uint8_t> none((size_t)N, 0);
+        const double W = weight_sum(g, none, 2);
+        transform_slots(g, sel, true, u, v);
+        std::vector<uint8_t> flags((size_t)N, 0);
+        for (int64_t x : sel) flags[(size_t)x] = 1;
+        ub = upd_buf(g);
+        KC_CK(g, cudaMemcpyAsync(ub.flags, flags.data(), flags.size(), cudaMemcpyHostToDevice,
+                                 g->stream));
+        KC_CK(g, launch_weight_rescale(g->d_w, ub.flags, N, ub.sums, R * W, (1.0 - R) * W,
+                                       g->stream));
+        KC_CK(g, cudaStreamSynchronize(g->stream));
+        g->t_update.launches += 2;
+    }
+    if (g->cfg.refresh_after_update) refresh_slots(g, all_slots(g));
+}
+
+void apply_delete(kc_graph *g, int32_t u, int32_t v, int32_t mode) {
+    const int64_t N = g->pool;
+    UpdBuf ub = upd_buf(g);
+    KC_CK(g, launch_contains_edge(g->n, N, g->d_parents, u, v, ub.flags, g->stream));
+    std::vector<uint8_t> flags((size_t)N, 0);
+    KC_CK(g, cudaMemcpyAsync(flags.data(), ub.flags, (size_t)N, cudaMemcpyDeviceToHost, g->stream));
+    int32_t pu = 0, pv = 0;
+    KC_CK(g, cudaMemcpyAsync(&pu, g->d_p0 + u, sizeof(int32_t), cudaMemcpyDeviceToHost, g->stream));
+    KC_CK(g, cudaMemcpyAsync(&pv, g->d_p0 + v, sizeof(int32_t), cudaMemcpyDeviceToHost, g->stream));
+    KC_CK(g, cudaStreamSynchronize(g->stream));
+    g->t_update.launches += 1;
+    std::vector<int64_t> hit;
+    for (int64_t i = 0; i < N; ++i)
+        if (flags[(size_t)i]) hit.push_back(i);
+    const bool tau0_hit = (pu == v) || (pv == u);
+    double w_org = 0.0;
+    if (mode == KC_UPDATE_ISM) w_org = weight_sum(g, flags, 0);
+    mutate_csr(g->h_row_off, g->h_col, u, v, false);
+    upload_graph(g);
+    if (tau0_hit) {
+        int nl = 0;
+        build_tau0(g, nl);
+        traverse_tau0(g, nl);
+        g->t_update.launches += nl;
+    }
+    if (mode == KC_UPDATE_BSM) {
+        resample_slots(g, hit, false, u, v);
+    } else {
+        transform_slots(g, hit, false, u, v);
+        ub = upd_buf(g);
+        KC_CK(g, cudaMemcpyAsync(ub.flags, flags.data(), flags.size(), cudaMemcpyHostToDevice,
+                                 g->stream));
+        KC_CK(g, launch_weight_rescale(g->d_w, ub.flags, N, ub.sums, w_org, -1.0, g->stream));
+        KC_CK(g, cudaStreamSynchronize(g->stream));
+        g->t_update.launches += 2;
+    }
+    if (g->cfg.refresh_after_update || tau0_hit) refresh_slots(g, all_slots(g));
 }
 
 double inv_normal_upper(double p_upper) {
@@ -416,6 +821,7 @@ kc_status kc_graph_destroy(kc_graph *g) {
     dfree(g->d_sid);
     dfree(g->d_parents);
     dfree(g->d_ws);
+    if (g->d_ub) cudaFree(g->d_ub);
     dfree(g->d_stack);
     dfree(g->d_sorder);
     dfree(g->d_err);
@@ -475,6 +881,7 @@ kc_status kc_graph_create(int64_t n, const int64_t *row_off, const int32_t *col,
 
         dalloc(g, &g->d_row_off, n + 1);
         dalloc(g, &g->d_col, twom);
+        g->col_cap = (size_t)twom;
         dalloc(g, &g->d_deg, n);
         dalloc(g, &g->d_rec, n);
         dalloc(g, &g->d_p0, n);
@@ -522,33 +929,8 @@ kc_status kc_graph_create(int64_t n, const int64_t *row_off, const int32_t *col,
             g->root = (int32_t)(0xFFFFFFFFull - (best & 0xFFFFFFFFull));
         }
         gv.root = g->root;
-        // BFS levels, one launch per level
-        KC_CK(g, launch_bfs_init(n, g->root, g->d_level0, g->stream));
-        ++launches;
-        int32_t *d_changed = (int32_t *)g->d_scratch;
-        int32_t lev = 0;
-        for (;; ++lev) {
-            KC_CK(g, cudaMemsetAsync(d_changed, 0, sizeof(int32_t), g->stream));
-            KC_CK(g, launch_bfs_level(gv, lev, g->d_level0, d_changed, g->stream));
-            ++launches;
-            int32_t changed = 0;
-            KC_CK(g, cudaMemcpyAsync(&changed, d_changed, sizeof(changed), cudaMemcpyDeviceToHost,
-                                     g->stream));
-            KC_CK(g, cudaStreamSynchronize(g->stream));
-            if (!changed) break;
-            if (lev > n) throw Fail{KC_ERR_CUDA};
-        }
-        g->ecc = lev;
-        gv.ecc = lev;
-        int32_t *d_unreached = (int32_t *)g->d_scratch;
-        KC_CK(g, cudaMemsetAsync(d_unreached, 0, sizeof(int32_t), g->stream));
-        KC_CK(g, launch_bfs_parent(gv, g->d_level0, g->d_p0, d_unreached, g->stream));
-        ++launches;
-        int32_t unreached = 0;
-        KC_CK(g, cudaMemcpyAsync(&unreached, d_unreached, sizeof(int32_t), cudaMemcpyDeviceToHost,
-                                 g->stream));
-        KC_CK(g, cudaStreamSynchronize(g->stream));
-        if (unreached) throw Fail{KC_ERR_DISCONNECTED};
+        build_tau0(g, launches);
+        gv.ecc = g->ecc;
         // Start order of the concurrent walkers: a fixed pseudo-random
         // permutation (vertices sorted by a 32-bit mix of their id), so that the
         // 32 walkers of a tree start far apart and rarely block each other.  Any
@@ -580,24 +962,7 @@ kc_status kc_graph_create(int64_t n, const int64_t *row_off, const int32_t *col,
             const long double bound = 4.0L * (long double)g->m * (long double)g->m * (long double)g->ecc;
             if (bound >= 4611686018427387904.0L) throw Fail{KC_ERR_OVERFLOW};
         }
-        // tau0 traversal with the same passes as the sampled trees (B = 1)
-        {
-            Plan p;
-            p.BW = 1;
-            p.BT = 1;
-            ensure_ws(g, p);
-            Carved c = carve(g, p);
-            WaveView w = c.wv;
-            w.B = 1;
-            KC_CK(g, launch_tau0_words(n, g->d_p0, g->d_level0, w.word, g->stream));
-            KC_CK(g, launch_level_order(n, g->ecc, g->d_level0, w.din, w.ord, g->stream));
-            int nl = 0;
-            KC_CK(g, launch_traverse(gv, w, false, g->stream, &nl));
-            KC_CK(g, launch_out_from_size(n, w.din, w.size, g->d_out0, g->stream));
-            KC_CK(g, cudaMemcpyAsync(g->d_in0, w.din, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice,
-                                     g->stream));
-            launches += 4 + nl;
-        }
+        traverse_tau0(g, launches);
         ph.done(launches);
         // TTF variant (Theorem 8: O(n min(Delta, log n)))
         int lg = 0;
@@ -740,7 +1105,63 @@ kc_status kc_get_tree(kc_graph *g, int64_t sample, int32_t *parent, int32_t *dep
                       int32_t *dfn_in, int32_t *dfn_out, int64_t *vol, int64_t *f,
                       int64_t *steps) {
     if (!g || sample < 0 || sample >= g->pool) return KC_ERR_INVALID_ARG;
-    if (g->h_modified[(size_t)sample]) return KC_ERR_NOT_RETAINED;
+    if (g->h_modified[(size_t)sample] && !g->cfg.keep_trees) return KC_ERR_NOT_RETAINED;
+    if (g->cfg.keep_trees) {
+        // retained tree (possibly drawn on an earlier version of the graph or
+        // changed by an update): traverse its stored parent array on the
+        // current graph; f and the step count are the pool's
+        try {
+            const int64_t n = g->n;
+            GraphView gv = view_of(g);
+            Plan p;
+            p.BW = 1;
+            p.BT = 1;
+            p.bit = g->ttf_variant == KC_TTF_BIT;
+            ensure_ws(g, p);
+            UpdBuf ub = upd_buf(g);
+            KC_CK(g, cudaMemcpyAsync(ub.slots, &sample, sizeof(int64_t), cudaMemcpyHostToDevice,
+                                     g->stream));
+            KC_CK(g, cudaMemsetAsync(g->d_err, 0, 2 * sizeof(uint32_t), g->stream));
+            Carved c = carve(g, p);
+            WaveView w = c.wv;
+            w.B = 1;
+            KC_CK(g, launch_prepare_from_parents(n, 1, g->root, g->d_parents, ub.slots, w,
+                                                 g->stream));
+            uint32_t hdr[2] = {0, 0};
+            KC_CK(g, cudaMemcpyAsync(hdr, g->d_err, sizeof(hdr), cudaMemcpyDeviceToHost, g->stream));
+            KC_CK(g, cudaStreamSynchronize(g->stream));
+            if (hdr[0]) check_err(g, "get_tree");
+            if (p.bit) {
+                ensure_stack(g, p, hdr[1]);
+                c = carve(g, p);
+                w = c.wv;
+                w.B = 1;
+            }
+            int nl = 0;
+            KC_CK(g, launch_traverse(gv, w, p.bit, g->stream, &nl));
+            if (p.bit) KC_CK(g, launch_ttf_bit(gv, w, g->stream));
+            else KC_CK(g, launch_ttf_scan(gv, w, g->stream));
+            check_err(g, "get_tree");
+            std::vector<uint64_t> word((size_t)n);
+            std::vector<int32_t> din((size_t)n), size((size_t)n);
+            KC_CK(g, cudaMemcpy(word.data(), w.word, sizeof(uint64_t) * n, cudaMemcpyDeviceToHost));
+            KC_CK(g, cudaMemcpy(din.data(), w.din, sizeof(int32_t) * n, cudaMemcpyDeviceToHost));
+            KC_CK(g, cudaMemcpy(size.data(), w.size, sizeof(int32_t) * n, cudaMemcpyDeviceToHost));
+            if (vol) KC_CK(g, cudaMemcpy(vol, w.vol, sizeof(int64_t) * n, cudaMemcpyDeviceToHost));
+            if (f) KC_CK(g, cudaMemcpy(f, g->d_f + sample, sizeof(int64_t), cudaMemcpyDeviceToHost));
+            if (steps) KC_CK(g, cudaMemcpy(steps, g->d_steps + sample, sizeof(int64_t),
+                                           cudaMemcpyDeviceToHost));
+            for (int64_t v = 0; v < n; ++v) {
+                if (parent) parent[v] = w_next(word[(size_t)v]);
+                if (depth) depth[v] = (int32_t)w_count(word[(size_t)v]);
+                if (dfn_in) dfn_in[v] = din[(size_t)v];
+                if (dfn_out) dfn_out[v] = din[(size_t)v] + size[(size_t)v] - 1;
+            }
+        } catch (Fail &e) {
+            return e.st;
+        }
+        return KC_OK;
+    }
     try {
         int64_t sid = 0;
         KC_CK(g, cudaMemcpy(&sid, g->d_sid + sample, sizeof(int64_t), cudaMemcpyDeviceToHost));
@@ -790,6 +1211,8 @@ kc_status kc_stats(kc_graph *g, kc_stats_t *out) {
     out->workspace_bytes = (int64_t)(g->ws_bytes + g->stack_bytes);
     out->updates_applied = g->updates_applied;
     out->trees_resampled = g->trees_resampled;
+    out->last_resistance = g->last_r;
+    out->last_cg_iters = g->last_cg_iters;
     out->ms_wilson = g->t_wilson.ms;
     out->ms_traverse = g->t_traverse.ms;
     out->ms_ttf = g->t_ttf.ms;
@@ -837,8 +1260,29 @@ kc_status kc_reset_timers(kc_graph *g) {
 kc_status kc_update(kc_graph *g, const kc_edge_op *ops, int64_t n_ops, int32_t mode) {
     if (!g || (n_ops > 0 && !ops) || n_ops < 0) return KC_ERR_INVALID_ARG;
     if (mode != KC_UPDATE_BSM && mode != KC_UPDATE_ISM) return KC_ERR_INVALID_ARG;
-    g->last_error = "kc_update: not available in this build";
-    return KC_ERR_INVALID_ARG;
+    if (!g->cfg.keep_trees) return KC_ERR_NOT_RETAINED;
+    if (g->pool == 0) return KC_ERR_NO_SAMPLES;
+    if (n_ops == 0) return KC_OK;
+    try {
+        const kc_status st = validate_batch(g, ops, n_ops);
+        if (st != KC_OK) return st;
+        KC_CK(g, cudaEventRecord(g->ev0, g->stream));
+        for (int64_t i = 0; i < n_ops; ++i) {
+            const kc_edge_op &o = ops[i];
+            if (o.op == 0) apply_insert(g, o.u, o.v, mode, o.r);
+            else apply_delete(g, o.u, o.v, mode);
+            ++g->updates_applied;
+            ++g->update_seq;
+        }
+        KC_CK(g, cudaEventRecord(g->ev1, g->stream));
+        KC_CK(g, cudaEventSynchronize(g->ev1));
+        float ms = 0.f;
+        KC_CK(g, cudaEventElapsedTime(&ms, g->ev0, g->ev1));
+        g->t_update.ms += ms;
+    } catch (Fail &f) {
+        return f.st;
+    }
+    return KC_OK;
 }
 
 }  // extern "C"

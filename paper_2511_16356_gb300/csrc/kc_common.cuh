@@ -139,6 +139,7 @@ struct WaveView {
     int32_t *maxdepth;       // [1] largest tree depth seen in the wave
     int32_t *stack;          // [B][stack_cap] x 4 int32 DFS stack (BIT variant)
     int64_t stack_cap;       // entries per tree
+    int32_t pos0 = 1;        // vertices already placed in ord before the walk
 };
 
 // ---------------------------------------------------------------------------
@@ -185,6 +186,9 @@ struct kc_graph {
     int32_t *d_stack = nullptr;     // BIT-variant DFS stacks, [trees][cap] x int4
     size_t stack_bytes = 0;
     int32_t *d_sorder = nullptr;    // start order of the concurrent walkers
+    void *d_ub = nullptr;           // update buffers: slots, factors, selection, flags
+    size_t ub_bytes = 0;
+    size_t col_cap = 0;             // capacity of d_col (entries)
     int64_t ws_trees = 0;
     uint32_t *d_err = nullptr;
     void *d_scratch = nullptr;      // small reduction scratch
@@ -193,6 +197,8 @@ struct kc_graph {
     int64_t total_steps = 0;
     int64_t updates_applied = 0, trees_resampled = 0;
     int64_t update_seq = 0;
+    double last_r = 0.0;
+    int64_t last_cg_iters = 0;
     kc::PhaseTimer t_wilson, t_traverse, t_ttf, t_reduce, t_update, t_setup, t_init;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     std::string last_error;
@@ -230,6 +236,36 @@ cudaError_t launch_pool_reduce(const int64_t *f, const double *w, int64_t count,
                                void *scratch, cudaStream_t s);
 cudaError_t launch_words_from_parents(int64_t n, int64_t B, const int32_t *parents,
                                       uint64_t *word, cudaStream_t s);
+
+// Sample maintenance (k6_update.cu) and effective resistance (k8_resistance.cu).
+cudaError_t launch_edge_pre_init(int64_t n, int64_t B, int32_t u, int32_t v, uint64_t *word,
+                                 int32_t *ord, cudaStream_t s);
+cudaError_t launch_words_to_slots(int64_t n, int64_t B, const uint64_t *word, const int64_t *slot,
+                                  int32_t *pool_parents, int32_t r, int32_t top, uint32_t *err,
+                                  cudaStream_t s);
+cudaError_t launch_contains_edge(int64_t n, int64_t P, const int32_t *pool_parents, int32_t u,
+                                 int32_t v, uint8_t *flag, cudaStream_t s);
+cudaError_t launch_select(uint64_t seed, uint32_t seq, int64_t N, int64_t k, uint8_t *taken,
+                          int64_t *out, cudaStream_t s);
+cudaError_t launch_prepare_from_parents(int64_t n, int64_t B, int32_t root,
+                                        const int32_t *pool_parents, const int64_t *slot,
+                                        WaveView w, cudaStream_t s);
+cudaError_t launch_link_cut(const int64_t *row_off, const int32_t *col, WaveView w,
+                            const int64_t *slot, int32_t *pool_parents, double *factor, int32_t r,
+                            int32_t u, int32_t v, uint64_t seed, uint32_t seq, bool insert,
+                            cudaStream_t s);
+cudaError_t launch_scale_slots(double *w, const int64_t *slot, const double *factor, int64_t B,
+                               cudaStream_t s);
+cudaError_t launch_weight_rescale(double *w, const uint8_t *flag, int64_t P, double *sums,
+                                  double target_flagged, double target_rest, cudaStream_t s);
+cudaError_t launch_weight_sums(const double *w, const uint8_t *flag, int64_t P, double *sums,
+                               cudaStream_t s);
+cudaError_t launch_scatter_results(const int64_t *slot, int64_t B, const int64_t *f,
+                                   const int64_t *steps, const int64_t *sids, int64_t *pool_f,
+                                   int64_t *pool_steps, int64_t *pool_sid, cudaStream_t s);
+// R(u, v) = (e_u - e_v)^T L^+ (e_u - e_v) by Jacobi-preconditioned FP64 CG.
+cudaError_t resistance_cg(const GraphView &g, int32_t u, int32_t v, double tol, int64_t max_iter,
+                          double *R_out, int64_t *iters_out, int *launches, cudaStream_t s);
 
 // Result layout of launch_pool_reduce in `scratch`.
 struct PoolSums {

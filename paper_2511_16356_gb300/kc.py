@@ -66,6 +66,7 @@ _STATS_FIELDS = [
     ("launches_wave_init", ctypes.c_int64),
     ("f_sum_hi", ctypes.c_int64), ("f_sum_lo", ctypes.c_uint64),
     ("wf_sum", ctypes.c_double), ("w_sum", ctypes.c_double), ("x2_sum", ctypes.c_double),
+    ("last_resistance", ctypes.c_double), ("last_cg_iters", ctypes.c_int64),
 ]
 
 
