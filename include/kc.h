@@ -94,7 +94,13 @@ enum { KC_R_CG = 0,            /* FP64 conjugate gradients on the Laplacian, on 
 
 typedef struct {
     uint32_t struct_size;       /* sizeof(kc_config), for ABI growth              */
-    int32_t root;               /* -1: highest degree, smallest id on ties (Exp-III) */
+    int32_t root;               /* >= 0: this vertex.  -1: highest degree (Exp-III), ties
+                                   broken towards the centre: among the highest-degree
+                                   vertices the one minimising max(d(a,.), d(b,.),
+                                   d(c,.)) for a = farthest from the smallest-id
+                                   candidate, b = farthest from a, c = maximiser of
+                                   min(d(a,.), d(b,.)); smallest id among equals.
+                                   -2: highest degree, smallest id among ties.      */
     int32_t ttf_variant;        /* KC_TTF_*                                         */
     int32_t keep_trees;         /* 1: retain parent arrays (needed by kc_update,
                                    kc_get_tree of updated trees); 0: static mode      */

@@ -12,7 +12,8 @@ import threading
 import numpy as np
 
 __all__ = [
-    "build_oracle", "lib", "philox4x32_10", "bounded", "root", "bfs_tree", "Tau0",
+    "build_oracle", "lib", "philox4x32_10", "bounded", "root", "root_smallest_id", "bfs_tree",
+    "Tau0",
     "tau0", "wilson", "traverse", "f_naive", "f_alg1", "TreeOut", "tree",
     "sample_batch", "num_threads", "STEP_CAP_DEFAULT", "cond_wilson", "select", "link_cut",
     "cut_link",
@@ -55,6 +56,8 @@ def lib():
             L.orc_bounded.restype = c_u32
             L.orc_root.argtypes = [c_i64, vp]
             L.orc_root.restype = c_i32
+            L.orc_root_central.argtypes = [c_i64, vp, vp]
+            L.orc_root_central.restype = c_i32
             L.orc_bfs_tree.argtypes = [c_i64, vp, vp, c_i32, vp, vp]
             L.orc_bfs_tree.restype = c_i32
             L.orc_wilson.argtypes = [c_i64, vp, vp, c_i32, c_u64, c_u32, vp, vp, vp, c_i64]
@@ -104,6 +107,12 @@ def bounded(seed: int, c0: int, c1: int, c2: int, tag: int, s: int) -> int:
 
 
 def root(g) -> int:
+    """Highest degree, ties broken towards the double-sweep centre, then smallest id."""
+    return int(lib().orc_root_central(g.n, _p(g.row_off), _p(g.col)))
+
+
+def root_smallest_id(g) -> int:
+    """Highest degree, smallest id among ties."""
     return int(lib().orc_root(g.n, _p(g.row_off)))
 
 

@@ -23,9 +23,10 @@
  *     negation of the reverse-case add.
  *
  * Readings of the paper taken here (all listed with reasons in the design
- * notes): neighbours are indexed in ascending id order; ties in the root and
- * BFS-parent choice go to the smallest id; DFN visits children in ascending
- * id; the undo in the reverse case of Algorithm 1 negates its add.
+ * notes): neighbours are indexed in ascending id order; ties in the root choice
+ * go to the most central candidate (see orc_root_central), ties in the
+ * BFS-parent choice to the smallest id; DFN visits children in ascending id;
+ * the undo in the reverse case of Algorithm 1 negates its add.
  */
 #include <stdint.h>
 #include <stdlib.h>
@@ -102,6 +103,81 @@ int32_t orc_root(int64_t n, const int64_t *row_off) {
         if (d > bd) { bd = d; best = (int32_t)v; }
     }
     return best;
+}
+
+/* BFS levels from s (-1 when unreachable); returns the number of reached vertices */
+static int64_t bfs_levels(int64_t n, const int64_t *row_off, const int32_t *col, int32_t s,
+                          int32_t *level, int32_t *queue) {
+    for (int64_t v = 0; v < n; ++v) level[v] = -1;
+    int64_t head = 0, tail = 0;
+    level[s] = 0;
+    queue[tail++] = s;
+    while (head < tail) {
+        int32_t u = queue[head++];
+        for (int64_t e = row_off[u]; e < row_off[u + 1]; ++e) {
+            int32_t w = col[e];
+            if (level[w] < 0) { level[w] = level[u] + 1; queue[tail++] = w; }
+        }
+    }
+    return tail;
+}
+
+/* the smallest-id vertex of largest level */
+static int32_t farthest(int64_t n, const int32_t *level) {
+    int32_t best = 0;
+    for (int64_t v = 0; v < n; ++v)
+        if (level[v] > level[best]) best = (int32_t)v;
+    return best;
+}
+
+/*
+ * Highest-degree vertex, ties broken towards the centre of the graph (Exp-III
+ * picks the highest degree because it shortens the walks; the paper gives no
+ * tie-break).  With r0 the smallest-id highest-degree vertex: a = the vertex
+ * farthest from r0, b = the vertex farthest from a, c = the vertex maximising
+ * min(dist(a, .), dist(b, .)) (smallest id on ties); the root is the
+ * highest-degree vertex minimising max(dist(a, .), dist(b, .), dist(c, .)),
+ * smallest id among equals -- a three-source lower bound on the eccentricity.
+ * A unique highest-degree vertex is returned directly.  Returns -1 for a
+ * disconnected graph.
+ */
+int32_t orc_root_central(int64_t n, const int64_t *row_off, const int32_t *col) {
+    int32_t r0 = orc_root(n, row_off);
+    int64_t dmax = row_off[r0 + 1] - row_off[r0];
+    int64_t ties = 0;
+    for (int64_t v = 0; v < n; ++v) ties += (row_off[v + 1] - row_off[v]) == dmax;
+    int32_t *la = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+    int32_t *lb = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+    int32_t *lc = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+    int32_t *q = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+    int32_t r = -1;
+    if (bfs_levels(n, row_off, col, r0, la, q) == n) {
+        if (ties == 1) {
+            r = r0;
+        } else {
+            int32_t a = farthest(n, la);
+            bfs_levels(n, row_off, col, a, la, q);
+            int32_t b = farthest(n, la);
+            bfs_levels(n, row_off, col, b, lb, q);
+            int32_t c = 0;
+            for (int64_t v = 0; v < n; ++v) {
+                int32_t mv = la[v] < lb[v] ? la[v] : lb[v];
+                int32_t mc = la[c] < lb[c] ? la[c] : lb[c];
+                if (mv > mc) c = (int32_t)v;
+            }
+            bfs_levels(n, row_off, col, c, lc, q);
+            int32_t best = -1;
+            for (int64_t v = 0; v < n; ++v) {
+                if (row_off[v + 1] - row_off[v] != dmax) continue;
+                int32_t e = la[v];
+                if (lb[v] > e) e = lb[v];
+                if (lc[v] > e) e = lc[v];
+                if (r < 0 || e < best) { r = (int32_t)v; best = e; }
+            }
+        }
+    }
+    free(la); free(lb); free(lc); free(q);
+    return r;
 }
 
 /*

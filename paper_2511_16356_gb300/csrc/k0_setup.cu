@@ -139,9 +139,44 @@ __global__ void k_level_scatter(int64_t n, const int32_t *level, int32_t *offs, 
     if (v < n) ord[atomicAdd(offs + level[v], 1)] = (int32_t)v;
 }
 
+// max over v of (score << 32 | (2^32 - 1 - v)): largest score, smallest id.
+// mode 0: score = level a; mode 1: score = min(level a, level b)
+__global__ void k_argmax_score(int64_t n, const int32_t *la, const int32_t *lb, int mode,
+                               unsigned long long *best) {
+    const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= n) return;
+    const int32_t sc = mode == 0 ? la[v] : min(la[v], lb[v]);
+    atomicMax(best, ((unsigned long long)(uint32_t)sc << 32) | (0xFFFFFFFFull - (unsigned long long)v));
+}
+
+// among vertices of degree dmax: min of (max(la, lb, lc) << 32 | v); also counts them
+__global__ void k_central_pick(int64_t n, const int32_t *deg, int32_t dmax, const int32_t *la,
+                               const int32_t *lb, const int32_t *lc, unsigned long long *best,
+                               int32_t *ties) {
+    const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= n || deg[v] != dmax) return;
+    atomicAdd(ties, 1);
+    if (!la) return;
+    const int32_t e = max(la[v], max(lb[v], lc[v]));
+    atomicMin(best, ((unsigned long long)(uint32_t)e << 32) | (unsigned long long)v);
+}
+
 inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
 }  // namespace
+
+cudaError_t launch_argmax_score(int64_t n, const int32_t *la, const int32_t *lb, int mode,
+                                unsigned long long *best, cudaStream_t s) {
+    k_argmax_score<<<blocks_for(n, 256), 256, 0, s>>>(n, la, lb, mode, best);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_central_pick(int64_t n, const int32_t *deg, int32_t dmax, const int32_t *la,
+                                const int32_t *lb, const int32_t *lc, unsigned long long *best,
+                                int32_t *ties, cudaStream_t s) {
+    k_central_pick<<<blocks_for(n, 256), 256, 0, s>>>(n, deg, dmax, la, lb, lc, best, ties);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_build_records(const GraphView &g, VRec *rec, int32_t *deg, cudaStream_t s) {
     k_build_records<<<blocks_for(g.n, 256), 256, 0, s>>>(g, rec, deg);

@@ -297,6 +297,82 @@ void run_wave(kc_graph *g, Plan &p, int64_t B, int64_t sid0) {
 }
 
 
+
+// BFS levels from src into `level` (one launch per level)
+void bfs_levels_dev(kc_graph *g, int32_t src, int32_t *level, int &launches) {
+    GraphView gv = view_of(g);
+    KC_CK(g, launch_bfs_init(g->n, src, level, g->stream));
+    ++launches;
+    int32_t *d_changed = (int32_t *)g->d_scratch;
+    for (int32_t lev = 0;; ++lev) {
+        KC_CK(g, cudaMemsetAsync(d_changed, 0, sizeof(int32_t), g->stream));
+        KC_CK(g, launch_bfs_level(gv, lev, level, d_changed, g->stream));
+        ++launches;
+        int32_t changed = 0;
+        KC_CK(g, cudaMemcpyAsync(&changed, d_changed, sizeof(changed), cudaMemcpyDeviceToHost,
+                                 g->stream));
+        KC_CK(g, cudaStreamSynchronize(g->stream));
+        if (!changed) break;
+        if (lev > g->n) throw Fail{KC_ERR_CUDA};
+    }
+}
+
+unsigned long long argmax_dev(kc_graph *g, const int32_t *la, const int32_t *lb, int mode,
+                              int &launches) {
+    unsigned long long *d = (unsigned long long *)g->d_scratch + 8;
+    KC_CK(g, cudaMemsetAsync(d, 0, sizeof(unsigned long long), g->stream));
+    KC_CK(g, launch_argmax_score(g->n, la, lb, mode, d, g->stream));
+    ++launches;
+    unsigned long long h = 0;
+    KC_CK(g, cudaMemcpyAsync(&h, d, sizeof(h), cudaMemcpyDeviceToHost, g->stream));
+    KC_CK(g, cudaStreamSynchronize(g->stream));
+    return h;
+}
+
+// Highest-degree vertex, ties broken towards the centre (the paper fixes no
+// tie-break; Exp-III prefers the root that shortens the walks): with r0 the
+// smallest-id highest-degree vertex, a the vertex farthest from r0, b the
+// vertex farthest from a and c the vertex maximising min(dist(a,.), dist(b,.)),
+// the root minimises max(dist(a,.), dist(b,.), dist(c,.)) over the
+// highest-degree vertices, smallest id among equals.  Unique maximum: r0.
+int32_t central_root(kc_graph *g, int32_t r0, int &launches) {
+    int32_t dmax = 0;
+    KC_CK(g, cudaMemcpy(&dmax, g->d_deg + r0, sizeof(int32_t), cudaMemcpyDeviceToHost));
+    int32_t *d_ties = (int32_t *)g->d_scratch + 32;
+    unsigned long long *d_best = (unsigned long long *)g->d_scratch + 24;
+    KC_CK(g, cudaMemsetAsync(d_ties, 0, sizeof(int32_t), g->stream));
+    KC_CK(g, launch_central_pick(g->n, g->d_deg, dmax, nullptr, nullptr, nullptr, d_best, d_ties,
+                                 g->stream));
+    ++launches;
+    int32_t ties = 0;
+    KC_CK(g, cudaMemcpyAsync(&ties, d_ties, sizeof(int32_t), cudaMemcpyDeviceToHost, g->stream));
+    KC_CK(g, cudaStreamSynchronize(g->stream));
+    if (ties <= 1) return r0;
+    int32_t *lv = nullptr;
+    dalloc(g, &lv, (size_t)(3 * g->n));
+    int32_t *la = lv, *lb = lv + g->n, *lc = lv + 2 * g->n;
+    try {
+        bfs_levels_dev(g, r0, la, launches);
+        const int32_t a = (int32_t)(0xFFFFFFFFull - (argmax_dev(g, la, la, 0, launches) & 0xFFFFFFFFull));
+        bfs_levels_dev(g, a, la, launches);
+        const int32_t b = (int32_t)(0xFFFFFFFFull - (argmax_dev(g, la, la, 0, launches) & 0xFFFFFFFFull));
+        bfs_levels_dev(g, b, lb, launches);
+        const int32_t c = (int32_t)(0xFFFFFFFFull - (argmax_dev(g, la, lb, 1, launches) & 0xFFFFFFFFull));
+        bfs_levels_dev(g, c, lc, launches);
+        KC_CK(g, cudaMemsetAsync(d_best, 0xFF, sizeof(unsigned long long), g->stream));
+        KC_CK(g, launch_central_pick(g->n, g->d_deg, dmax, la, lb, lc, d_best, d_ties, g->stream));
+        ++launches;
+        unsigned long long best = 0;
+        KC_CK(g, cudaMemcpyAsync(&best, d_best, sizeof(best), cudaMemcpyDeviceToHost, g->stream));
+        KC_CK(g, cudaStreamSynchronize(g->stream));
+        dfree(lv);
+        return (int32_t)(best & 0xFFFFFFFFull);
+    } catch (Fail &) {
+        dfree(lv);
+        throw;
+    }
+}
+
 // tau0 = BFS tree from g->root over the current device graph (parent = the
 // smallest-id neighbour one level closer), level-synchronous, one launch per
 // level; sets g->ecc.  Throws KC_ERR_DISCONNECTED if a vertex is unreached.
@@ -927,6 +1003,7 @@ kc_status kc_graph_create(int64_t n, const int64_t *row_off, const int32_t *col,
             KC_CK(g, cudaMemcpyAsync(&best, d_best, sizeof(best), cudaMemcpyDeviceToHost, g->stream));
             KC_CK(g, cudaStreamSynchronize(g->stream));
             g->root = (int32_t)(0xFFFFFFFFull - (best & 0xFFFFFFFFull));
+            if (cfg.root == -1) g->root = central_root(g, g->root, launches);
         }
         gv.root = g->root;
         build_tau0(g, launches);

@@ -211,6 +211,11 @@ cudaError_t launch_build_records(const GraphView &g, VRec *rec, int32_t *deg, cu
 cudaError_t launch_validate(const GraphView &g, uint32_t *flags, cudaStream_t s);
 cudaError_t launch_root(const GraphView &g, unsigned long long *best, cudaStream_t s);
 cudaError_t launch_bfs_init(int64_t n, int32_t r, int32_t *level, cudaStream_t s);
+cudaError_t launch_argmax_score(int64_t n, const int32_t *la, const int32_t *lb, int mode,
+                                unsigned long long *best, cudaStream_t s);
+cudaError_t launch_central_pick(int64_t n, const int32_t *deg, int32_t dmax, const int32_t *la,
+                                const int32_t *lb, const int32_t *lc, unsigned long long *best,
+                                int32_t *ties, cudaStream_t s);
 cudaError_t launch_bfs_level(const GraphView &g, int32_t lev, int32_t *level, int32_t *changed,
                              cudaStream_t s);
 cudaError_t launch_bfs_parent(const GraphView &g, const int32_t *level, int32_t *p0,

@@ -161,7 +161,28 @@ def test_root_highest_degree_smallest_id():
     g = S.csr_from_edges(6, [0, 1, 1, 2, 3, 3, 4], [5, 2, 4, 4, 4, 5, 5])
     deg = g.deg
     want = int(np.flatnonzero(deg == deg.max())[0])
-    assert O.root(g) == want
+    assert O.root_smallest_id(g) == want
+    # a unique highest-degree vertex is the root under both tie rules
+    st = S.star(7)
+    assert O.root(st) == O.root_smallest_id(st) == 0
+
+
+@pytest.mark.parametrize("n", [9, 10, 31])
+def test_central_root_on_paths_is_a_middle_vertex(n):
+    """All interior vertices of a path tie on degree; the centre (eccentricity
+    minimiser) of a path is its middle vertex (one of the two middles for even n)."""
+    g = S.path(n)
+    r = O.root(g)
+    assert r in ((n - 1) // 2, n // 2)
+    assert O.root_smallest_id(g) == 1
+
+
+def test_central_root_shortens_the_bfs_tree_on_grids():
+    g = S.grid_perturbed(41, 41, 0.25, 3)
+    near = O.tau0(g)
+    far = O.tau0(g, O.root_smallest_id(g))
+    assert g.deg[near.r] == g.deg.max()
+    assert near.ecc < 0.7 * far.ecc
 
 
 @pytest.mark.parametrize("seed", [0, 1, 2])
