@@ -76,7 +76,7 @@ __global__ void __launch_bounds__(128) k_wilson(GraphView g, WaveView w, uint64_
                 break;
             }
             const uint64_t wv = word[v];
-            const VRec rv = rec[v];
+            const VRec rv = load_rec(rec + v);
             if (w_in_tree(wv)) {
                 u = s;
                 len = 0;

@@ -67,22 +67,26 @@ __global__ void __launch_bounds__(256) k_ttf_scan(GraphView g, WaveView w) {
     }
 }
 
-// index of the c-th node of the Fenwick update chain starting at i (1-based)
-__device__ __forceinline__ int64_t up_chain(int64_t i, int c) {
-    for (int k = 0; k < c; ++k) i += i & (-i);
-    return i;
+// Fenwick point update at 1-based index i, the warp's lanes sharing the chain.
+// With j = i - 1 the chain is j, j | (j + 1), ...: its k-th node sets the k
+// lowest zero bits of j, i.e. equals j | (2^(b+1) - 1) where b is the k-th
+// zero bit.  So lane b (b < 31) owns the node of zero bit b of j and lane 31
+// owns node 0 (j itself); every node is visited exactly once.
+__device__ __forceinline__ void bit_point_add(int64_t *bit, int64_t n, int lane, int64_t i,
+                                              long long val) {
+    const uint32_t j = (uint32_t)(i - 1);  // host guarantees n < 2^31
+    int64_t node;
+    if (lane == 31) node = (int64_t)j + 1;
+    else if ((j >> lane) & 1u) node = -1;
+    else node = (int64_t)(j | ((2u << lane) - 1u)) + 1;
+    if (node >= 1 && node <= n) atomicAdd((unsigned long long *)(bit + node), (unsigned long long)val);
 }
 
 // range add [l, r] (0-based positions) += val, as two point updates
 __device__ __forceinline__ void bit_range_add(int64_t *bit, int64_t n, int lane, int32_t l,
                                               int32_t r, long long val) {
-    // the chain strictly increases, so lane c owns its c-th node exclusively
-    const int64_t a = up_chain((int64_t)l + 1, lane);
-    if (a <= n) atomicAdd((unsigned long long *)(bit + a), (unsigned long long)val);
-    if ((int64_t)r + 2 <= n) {
-        const int64_t b = up_chain((int64_t)r + 2, lane);
-        if (b <= n) atomicAdd((unsigned long long *)(bit + b), (unsigned long long)(-val));
-    }
+    bit_point_add(bit, n, lane, (int64_t)l + 1, val);
+    if ((int64_t)r + 2 <= n) bit_point_add(bit, n, lane, (int64_t)r + 2, -val);
 }
 
 __global__ void __launch_bounds__(128) k_ttf_bit(GraphView g, WaveView w) {

@@ -45,9 +45,9 @@ __device__ __forceinline__ void philox4x32_10(uint32_t c0, uint32_t c1, uint32_t
     out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
 }
 
-// Uniform integer in [0, s), s >= 1.
-__device__ __forceinline__ uint32_t bounded_draw(uint64_t seed, uint32_t c0, uint32_t c1,
-                                                 uint32_t c2, uint32_t tag, uint32_t s) {
+// Uniform integer in [0, s), s >= 1: all four words and the retry counter.
+static __device__ __noinline__ uint32_t bounded_draw_full(uint64_t seed, uint32_t c0, uint32_t c1,
+                                                   uint32_t c2, uint32_t tag, uint32_t s) {
     const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
     for (uint32_t retry = 0; retry < (1u << 24); ++retry) {
         uint32_t w[4];
@@ -66,6 +66,18 @@ __device__ __forceinline__ uint32_t bounded_draw(uint64_t seed, uint32_t c0, uin
     return 0;
 }
 
+// Same result as bounded_draw_full.  Fast path: word 0 of the first block is
+// accepted outright when the low half of x*s is >= s (the rejection threshold
+// (2^32 - s) mod s is below s), which fails with probability s / 2^32.
+__device__ __forceinline__ uint32_t bounded_draw(uint64_t seed, uint32_t c0, uint32_t c1,
+                                                 uint32_t c2, uint32_t tag, uint32_t s) {
+    uint32_t w[4];
+    philox4x32_10(c0, c1, c2, tag << 24, (uint32_t)seed, (uint32_t)(seed >> 32), w);
+    const uint64_t m = (uint64_t)w[0] * (uint64_t)s;
+    if (__builtin_expect((uint32_t)m >= s, 1)) return (uint32_t)(m >> 32);
+    return bounded_draw_full(seed, c0, c1, c2, tag, s);
+}
+
 // ---------------------------------------------------------------------------
 // Vertex record used by the walk: one 32-byte sector per vertex holding the
 // degree, the CSR offset and the first kInline neighbours, so a step on a
@@ -79,6 +91,22 @@ struct __align__(32) VRec {
     int32_t nbr[kInline];
 };
 static_assert(sizeof(VRec) == 32, "VRec must be one sector");
+
+// the record as two 16-byte loads through the read-only data path
+__device__ __forceinline__ VRec load_rec(const VRec *p) {
+    const uint4 *q = reinterpret_cast<const uint4 *>(p);
+    const uint4 a = __ldg(q), b = __ldg(q + 1);
+    VRec r;
+    r.deg = (int32_t)a.x;
+    r.off_lo = a.y;
+    r.off_hi = a.z;
+    r.nbr[0] = (int32_t)a.w;
+    r.nbr[1] = (int32_t)b.x;
+    r.nbr[2] = (int32_t)b.y;
+    r.nbr[3] = (int32_t)b.z;
+    r.nbr[4] = (int32_t)b.w;
+    return r;
+}
 
 // ---------------------------------------------------------------------------
 // Per-tree vertex word of the walker (8 bytes):
