@@ -125,14 +125,9 @@ def dist_setup():
 
 
 def reduce_max(dist, x: float) -> float:
-    if dist is None:
-        return x
-    import torch
+    from paper_2511_16356_gb300.dist import max_over_ranks
 
-    dev = "cuda" if torch.cuda.is_available() and dist.get_backend() == "nccl" else "cpu"
-    t = torch.tensor([x], dtype=torch.float64, device=dev)
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    return float(t.item())
+    return x if dist is None else max_over_ranks(x)
 
 
 def barrier(dist):
@@ -227,10 +222,11 @@ def main():
     n = g.n
     T = args.trees
     WT = args.warmup_trees or T
-    ids_per_rank = 1 << 28
+    from paper_2511_16356_gb300.dist import rank_sample_base
+
     cfg = kc.kc_config_default()
     cfg.keep_trees = 0
-    cfg.sample_id_base = rank * ids_per_rank
+    cfg.sample_id_base = rank_sample_base(rank, ws)
     cfg.step_cap = args.step_cap_per_n * n
     cfg.walker = {"auto": kc.KC_WALK_AUTO, "warp": kc.KC_WALK_WARP,
                   "lane": kc.KC_WALK_LANE}[args.walker]
