@@ -135,14 +135,14 @@ def barrier(dist):
         dist.barrier()
 
 
-def oracle_baseline(g, trees: int, seed: int, threads: int = 0):
+def oracle_baseline(g, trees: int, seed: int, threads: int = 0, first: int = 0):
     """The CPU oracle as it stands: Wilson + traversal + Algorithm 1 over a
     bounded sample of sample ids, OpenMP across trees on the host cores."""
     import oracle as O
 
     t0 = O.tau0(g)
     t = time.perf_counter()
-    f, steps = O.sample_batch(g, t0, seed, 0, trees, threads=threads)
+    f, steps = O.sample_batch(g, t0, seed, first, trees, threads=threads)
     el = time.perf_counter() - t
     return trees / el, el, O.num_threads() if threads <= 0 else threads
 
@@ -182,6 +182,9 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+WALKER_NAMES = {1: "lane", 2: "warp", 3: "hybrid"}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -198,7 +201,12 @@ def main():
     ap.add_argument("--ref-trees", type=int, default=32)
     ap.add_argument("--step-cap-per-n", type=int, default=256,
                     help="Wilson departures allowed per tree, in units of n")
-    ap.add_argument("--walker", default="auto", choices=["auto", "warp", "lane"])
+    ap.add_argument("--walker", default="auto", choices=["auto", "warp", "lane", "hybrid"])
+    ap.add_argument("--hybrid-prefix", type=int, default=0,
+                    help="hybrid walker: lane-phase starts in thousandths of n (0: library default)")
+    ap.add_argument("--hybrid-tail", type=int, default=0,
+                    help="hybrid walker: hand-off share of finished trees, in thousandths "
+                         "(0: library default)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-tte", action="store_true")
@@ -229,7 +237,9 @@ def main():
     cfg.sample_id_base = rank_sample_base(rank, ws)
     cfg.step_cap = args.step_cap_per_n * n
     cfg.walker = {"auto": kc.KC_WALK_AUTO, "warp": kc.KC_WALK_WARP,
-                  "lane": kc.KC_WALK_LANE}[args.walker]
+                  "lane": kc.KC_WALK_LANE, "hybrid": kc.KC_WALK_HYBRID}[args.walker]
+    cfg.hybrid_prefix_permille = args.hybrid_prefix
+    cfg.hybrid_tail_permille = args.hybrid_tail
     G = kc.KemenyGraph.from_graph(g, cfg, stream=stream.cuda_stream)
     st0 = G.stats()
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.int32, device="cuda")
@@ -279,7 +289,9 @@ def main():
     per_launch_s = dom_ms / 1000.0 / max(1, dom_launches)
     achieved = per_launch_bytes / per_launch_s / 1e9
     launches = sum(st[k] for k in st if k.startswith("launches_") and k != "launches_setup")
-    kernel_name = {"wilson": "k_wilson", "traverse": "k_bottom_up/k_sibling_offsets/k_top_down",
+    kernel_name = {"wilson": {kc.KC_WALK_LANE: "k_wilson", kc.KC_WALK_WARP: "k_wilson_warp",
+                              kc.KC_WALK_HYBRID: "k_wilson+k_wilson_warp"}[st["walker"]],
+                   "traverse": "k_bottom_up/k_sibling_offsets/k_top_down",
                    "ttf_bit": "k_ttf_bit", "ttf_scan": "k_ttf_scan"}[dom]
     phase_ms = {k: round(v[0], 3) for k, v in phases.items()}
     phase_ms["wave_init"] = round(st["ms_wave_init"], 3)
@@ -296,7 +308,7 @@ def main():
                    "l2": "flushed between timed steps (258 MB write); per-step working set "
                          f"{st['workspace_bytes'] / 1e9:.1f} GB",
                    "ttf": "BIT" if st["ttf_variant"] == kc.KC_TTF_BIT else "SCAN",
-                   "walker": "lane" if st["walker"] == kc.KC_WALK_LANE else "warp",
+                   "walker": WALKER_NAMES[st["walker"]],
                    "trees_in_flight": st["trees_in_flight"]},
         "roofline": {"bound": "hbm", "kernel": kernel_name, "achieved": achieved, "peak": peak,
                      "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
@@ -317,6 +329,8 @@ def main():
         cfg2.keep_trees = 0
         cfg2.step_cap = cfg.step_cap
         cfg2.walker = cfg.walker
+        cfg2.hybrid_prefix_permille = cfg.hybrid_prefix_permille
+        cfg2.hybrid_tail_permille = cfg.hybrid_tail_permille
         cfg2.batch_trees = 1024
         H = kc.KemenyGraph.from_graph(g, cfg2, stream=stream.cuda_stream)
         torch.cuda.synchronize()
@@ -359,10 +373,17 @@ def main():
 
     # ---- the CPU oracle on the host cores (rank 0, N = 1 only)
     if not args.no_cpu_baseline and rank == 0 and ws == 1:
+        # a calibration batch, then enough further trees for about 15 s of work
         cores = os.cpu_count() or 1
         trees = max(2 * cores, 16)
-        v, el, used = oracle_baseline(g, trees, args.seed)
-        out["cpu_baseline"] = {"value": v, "unit": "trees/s", "cores": used, "kind": "oracle",
+        _, el, used = oracle_baseline(g, trees, args.seed)
+        if el < 10.0:
+            more = int(min(1 << 16, max(cores, trees * (15.0 - el) / max(el, 1e-3))))
+            more = (more + cores - 1) // cores * cores
+            _, el2, used = oracle_baseline(g, more, args.seed, first=trees)
+            trees, el = trees + more, el + el2
+        out["cpu_baseline"] = {"value": trees / el, "unit": "trees/s", "cores": used,
+                               "kind": "oracle",
                                "sample": f"{trees} trees (sample ids 0..{trees - 1}) of "
                                          f"{args.workload}, {el:.1f} s, OpenMP across trees"}
     if rank == 0:

@@ -83,10 +83,13 @@ enum { KC_STOP_CLT = 0,        /* z_{1-delta/2} s / sqrt(w) <= eps K_hat (1 - ep
 enum { KC_UPDATE_BSM = 0,      /* Algorithm 2 */
        KC_UPDATE_ISM = 1 };    /* Algorithm 3 */
 
-/* Wilson walkers per tree.  Both give identical trees and step counts. */
-enum { KC_WALK_AUTO = 0,       /* WARP when ecc(r) <= 2 log2 n, else LANE                */
+/* Wilson walkers per tree.  All give identical trees and step counts. */
+enum { KC_WALK_AUTO = 0,       /* WARP                                                    */
        KC_WALK_LANE = 1,       /* one sequential walker per tree (one lane)              */
-       KC_WALK_WARP = 2 };     /* 32 concurrent walkers per tree popping cycles in any order */
+       KC_WALK_WARP = 2,       /* 32 concurrent walkers per tree popping cycles in any order */
+       KC_WALK_HYBRID = 3 };   /* LANE for a prefix of the start order, then WARP for the
+                                  rest; LANE trees still running when a share of the
+                                  wave has finished are also handed to WARP          */
 
 /* Effective resistance source for insertions (Algorithm 2/3 "Compute R(u,v)"). */
 enum { KC_R_CG = 0,            /* FP64 conjugate gradients on the Laplacian, on the device */
@@ -119,6 +122,13 @@ typedef struct {
     double mem_fraction;        /* share of free device memory for workspaces (0: 0.6) */
     int64_t sample_id_base;     /* first sample id of the pool (0); ranks of a
                                    multi-GPU run use disjoint bases, ids < 2^32   */
+    int32_t hybrid_prefix_permille; /* KC_WALK_HYBRID: starts of the lane phase, in
+                                   thousandths of n (0: default 1000 = all; the
+                                   tail hand-off alone then moves work to WARP)     */
+    int32_t hybrid_tail_permille; /* KC_WALK_HYBRID: lane trees still running when
+                                   this many thousandths of the wave's trees have
+                                   finished continue as WARP trees (0: default 900;
+                                   >= 1000: never)                                  */
 } kc_config;
 
 /* Fill *cfg with the defaults listed above. */

@@ -18,7 +18,7 @@ namespace kc {
 
 namespace {
 
-enum : int { kSeek = 0, kWalk = 1, kCount = 2, kCommit = 3, kDone = 4 };
+enum : int { kSeek = 0, kWalk = 1, kCount = 2, kCommit = 3 };
 
 __global__ void k_wave_init(int64_t n, int64_t B, int32_t root, uint64_t *word, int32_t *ord) {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -27,9 +27,19 @@ __global__ void k_wave_init(int64_t n, int64_t B, int32_t root, uint64_t *word, 
     ord[t * n] = root;
 }
 
+// Starts are taken in the order sorder[0 .. n) (id order when sorder is null).
+// With rs_q set the lane may stop early, at a start boundary -- no walk in
+// flight, every vertex either in the tree or free with its departure count --
+// when it reaches order index q_stop, or when `done` (trees of the wave that
+// already finished) has reached stop_at.  It then saves the order index of its
+// next start and its order position in rs_q / rs_pos (rs_q = -1 for a
+// finished tree), and the 32-walker kernel resumes the tree from there.
 __global__ void __launch_bounds__(128) k_wilson(GraphView g, WaveView w, uint64_t seed,
                                                 const int64_t *__restrict__ sids,
-                                                int64_t step_cap) {
+                                                const int32_t *__restrict__ sorder,
+                                                int64_t step_cap, int32_t *rs_q, int32_t *rs_pos,
+                                                unsigned int *done, int64_t q_stop,
+                                                int64_t stop_at) {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= w.B) return;
     const int64_t n = g.n;
@@ -40,23 +50,24 @@ __global__ void __launch_bounds__(128) k_wilson(GraphView g, WaveView w, uint64_
 
     int64_t steps = 0;
     int32_t pos = w.pos0;  // ord[0 .. pos0) already placed (the root, or an edge)
+    int32_t q = 0;         // order index of the current start
     int32_t s = 0;         // current start vertex
     int32_t u = 0;         // walker position (WALK) / path cursor (COUNT, COMMIT)
     uint64_t wu = 0;       // word of u (WALK)
     VRec ru;               // record of u (WALK)
+    ru.deg = 1;
     int32_t len = 0, i = 0, dh = 0, maxd = 0;
     int phase = kSeek;
+    bool stopped = false;
 
-    while (phase != kDone) {
-        if (phase == kSeek) {
-            if (s >= n) { phase = kDone; break; }
-            const uint64_t ws = word[s];
-            if (w_in_tree(ws)) { ++s; continue; }
-            u = s;
-            wu = ws;
-            ru = rec[s];
-            phase = kWalk;
-        } else if (phase == kWalk) {
+    // Every iteration: phase-specific arithmetic, then ONE gather (the word of
+    // one vertex, with its record when the lane may walk from it), then
+    // phase-specific resolution.  Lanes of a warp sit in different phases, so
+    // a gather per phase branch would serialise up to four memory round trips.
+    for (;;) {
+        int32_t a;
+        bool want_rec = true;
+        if (phase == kWalk) {
             const uint32_t k = bounded_draw(seed, (uint32_t)u, w_count(wu), sample, kTagWalk,
                                             (uint32_t)ru.deg);
             int32_t v;
@@ -64,48 +75,71 @@ __global__ void __launch_bounds__(128) k_wilson(GraphView g, WaveView w, uint64_
                 // register select instead of a dynamic index into the record
                 v = ru.nbr[0];
 #pragma unroll
-                for (int q = 1; q < kInline; ++q) v = (k == (uint32_t)q) ? ru.nbr[q] : v;
+                for (int z = 1; z < kInline; ++z) v = (k == (uint32_t)z) ? ru.nbr[z] : v;
             } else {
                 const uint64_t off = (uint64_t)ru.off_lo | ((uint64_t)ru.off_hi << 32);
                 v = g.col[off + k];
             }
             word[u] = w_make(v, w_count(wu) + 1, false);
-            if (++steps > step_cap) {
+            if (++steps > step_cap || w_count(wu) + 1 >= (1u << 25)) {
                 atomicOr(w.err, kErrStepLimit);
-                phase = kDone;
                 break;
             }
-            const uint64_t wv = word[v];
-            const VRec rv = load_rec(rec + v);
-            if (w_in_tree(wv)) {
+            a = v;
+        } else if (phase == kSeek) {
+            if (q >= n) break;
+            if (rs_q && (q >= q_stop || ((q & 255) == 0 && stop_at > 0 &&
+                                         (int64_t)*(volatile unsigned int *)done >= stop_at))) {
+                stopped = true;
+                break;
+            }
+            s = sorder ? sorder[q] : q;
+            a = s;
+        } else {  // kCount, kCommit: the path cursor
+            a = u;
+            want_rec = false;
+        }
+        const uint64_t wa = word[a];
+        VRec ra;
+        ra.deg = 1;
+        if (want_rec) ra = load_rec(rec + a);
+
+        if (phase == kWalk) {
+            if (w_in_tree(wa)) {
                 u = s;
                 len = 0;
                 phase = kCount;
             } else {
-                u = v;
-                wu = wv;
-                ru = rv;
+                u = a;
+                wu = wa;
+                ru = ra;
+            }
+        } else if (phase == kSeek) {
+            if (w_in_tree(wa)) {
+                ++q;
+            } else {
+                u = s;
+                wu = wa;
+                ru = ra;
+                phase = kWalk;
             }
         } else if (phase == kCount) {
             // length of the loop-erased path from s and the depth of its tree end
-            const uint64_t wx = word[u];
-            if (w_in_tree(wx)) {
-                dh = (int32_t)w_count(wx);
+            if (w_in_tree(wa)) {
+                dh = (int32_t)w_count(wa);
                 u = s;
                 i = 0;
                 phase = kCommit;
             } else {
                 ++len;
-                u = w_next(wx);
+                u = w_next(wa);
                 if (len > n || u < 0 || u >= n) {  // a path longer than n means corrupt state
                     atomicOr(w.err, kErrBadTree);
-                    phase = kDone;
                     break;
                 }
             }
         } else {  // kCommit
-            const uint64_t wx = word[u];
-            const int32_t nx = w_next(wx);
+            const int32_t nx = w_next(wa);
             const int32_t d = dh + len - i;
             word[u] = w_make(nx, (uint32_t)d, true);
             ord[pos + len - 1 - i] = u;
@@ -114,13 +148,18 @@ __global__ void __launch_bounds__(128) k_wilson(GraphView g, WaveView w, uint64_
             u = nx;
             if (i == len) {
                 pos += len;
-                ++s;
+                ++q;
                 phase = kSeek;
             }
         }
     }
     w.steps[t] = steps;
     atomicMax(w.maxdepth, maxd);
+    if (rs_q) {
+        rs_q[t] = stopped ? q : -1;
+        rs_pos[t] = pos;
+        if (!stopped) atomicAdd(done, 1u);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -171,12 +210,10 @@ __device__ __forceinline__ int32_t rec_neighbor(const VRec &r, const int32_t *co
     const uint64_t off = (uint64_t)r.off_lo | ((uint64_t)r.off_hi << 32);
     return col[off + k];
 }
-__device__ __forceinline__ uint64_t ld_word(const uint64_t *p) {
-    return (uint64_t)__ldcg((const unsigned long long *)p);
-}
-__device__ __forceinline__ void st_word(uint64_t *p, uint64_t v) {
-    __stcg((unsigned long long *)p, (unsigned long long)v);
-}
+// Plain (L1-cached) accesses: the words of a tree are shared by the lanes of
+// one warp only, and __syncwarp orders their stores before the next loads.
+__device__ __forceinline__ uint64_t ld_word(const uint64_t *p) { return *p; }
+__device__ __forceinline__ void st_word(uint64_t *p, uint64_t v) { *p = v; }
 
 enum : int {
     pIdle = 0,     // needs a start vertex
@@ -190,15 +227,24 @@ enum : int {
     pDone = 8
 };
 
-__global__ void __launch_bounds__(128) k_wilson_warp(GraphView g, WaveView w, uint64_t seed,
+// With rs_q set, warp t resumes wave tree t where k_wilson stopped it: at order
+// index rs_q[t] of the same start order and order position rs_pos[t], adding
+// to its step count (rs_q[t] < 0: the tree is finished and the warp exits).
+// Otherwise warp t samples tree t from scratch.
+__global__ void __launch_bounds__(128, 7) k_wilson_warp(GraphView g, WaveView w, uint64_t seed,
                                                      const int64_t *__restrict__ sids,
                                                      const int32_t *__restrict__ sorder,
-                                                     int64_t step_cap, int64_t iter_cap) {
+                                                     int64_t step_cap, int64_t iter_cap,
+                                                     const int32_t *__restrict__ rs_q,
+                                                     const int32_t *__restrict__ rs_pos) {
     const unsigned kFull = 0xFFFFFFFFu;
     const int lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
+    __shared__ int32_t xs_all[4][32];  // per warp: vertex each cycle lane's predecessor waits on
+    int32_t *xs = xs_all[threadIdx.x >> 5];
     const int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (t >= w.B) return;  // whole warp
+    if (t >= w.B) return;                   // whole warp
+    if (rs_q && rs_q[t] < 0) return;        // whole warp: finished by the lane walker
     const int64_t n = g.n;
     uint64_t *word = w.word + t * n;
     int32_t *ord = w.ord + t * n;
@@ -213,8 +259,8 @@ __global__ void __launch_bounds__(128) k_wilson_warp(GraphView g, WaveView w, ui
     rc.deg = 1;
     int32_t len = 0, i = 0, dh = 0, mypos = 0, maxd = 0;
     int64_t steps = 0;
-    int64_t next_start = 0;  // warp-uniform
-    int64_t pos = w.pos0;    // warp-uniform, ord[0 .. pos0) already placed
+    int64_t next_start = rs_q ? (int64_t)rs_q[t] : 0;  // warp-uniform
+    int64_t pos = rs_q ? (int64_t)rs_pos[t] : w.pos0;   // warp-uniform, ord[0 .. pos) placed
     bool bad = false;
 
     for (int64_t it = 0;; ++it) {
@@ -356,7 +402,7 @@ __global__ void __launch_bounds__(128) k_wilson_warp(GraphView g, WaveView w, ui
             if (i == len) ph = pIdle;
         }
         // ---- reserve slots of the parent-first order for paths that reached the tree
-        {
+        if (__any_sync(kFull, fin)) {
             int32_t v = fin ? len : 0;
             int32_t incl = v;
 #pragma unroll
@@ -373,35 +419,31 @@ __global__ void __launch_bounds__(128) k_wilson_warp(GraphView g, WaveView w, ui
             }
             pos += total;
         }
-        // ---- wait cycles: each lane that stays waiting points at the owner of its target
-        // (a cycle of waits persists until it is popped, so looking every 4th
-        // iteration only delays the pop a little and saves the shuffle chains)
+        // ---- wait cycles: each lane that stays waiting points at the owner of its
+        // target.  A lane lies on a cycle of this functional graph exactly when it
+        // is succ^32 of some lane (a 32-step path among 32 lanes must have entered
+        // a cycle, and succ^32 permutes each cycle), found by 5 doubling rounds.
         const int succ = (was_wait && ph == pWait && has_path && own && ownr != lane) ? ownr : -1;
-        const unsigned wm = __ballot_sync(kFull, succ >= 0);
-        if ((it & 3) == 0 && __popc(wm) >= 2) {
-            int y = lane;
-            bool on = false;
-#pragma unroll 4
-            for (int k = 0; k < 32; ++k) {
-                const int sy = __shfl_sync(kFull, succ, y < 0 ? lane : y);
-                y = (y < 0) ? -1 : sy;
-                if (y == lane) on = true;
+        if (__popc(__ballot_sync(kFull, succ >= 0)) >= 2) {
+            int z = succ;
+#pragma unroll
+            for (int r = 0; r < 5; ++r) {
+                const int zz = __shfl_sync(kFull, z, z < 0 ? lane : z);
+                z = z < 0 ? -1 : zz;
             }
-            on = on && succ >= 0;
-            const unsigned onm = __ballot_sync(kFull, on);
+            const unsigned onm = __reduce_or_sync(kFull, z >= 0 ? 1u << z : 0u);
             if (onm) {
-                int pred = -1;
-                for (int j = 0; j < 32; ++j) {
-                    const int sj = __shfl_sync(kFull, succ, j);
-                    if (((onm >> j) & 1u) && sj == lane) pred = j;
-                }
-                const int32_t xp = __shfl_sync(kFull, x, pred < 0 ? lane : pred);
+                // each lane on a cycle hands the vertex it waits on to its successor,
+                // whose path contains it: that lane pops the cycle segment after the
+                // vertex and re-departs from it
+                const bool on = (onm >> lane) & 1u;
+                if (on) xs[succ] = x;
+                __syncwarp();
                 if (on) {
-                    // the vertex my predecessor waits on is on my path: pop the
-                    // cycle segment after it and re-depart from it
-                    prew = xp;
+                    prew = xs[lane];
                     ph = pPopSet;
                 }
+                __syncwarp();
             }
         }
     }
@@ -412,7 +454,7 @@ __global__ void __launch_bounds__(128) k_wilson_warp(GraphView g, WaveView w, ui
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) md = max(md, __shfl_down_sync(kFull, md, o));
     if (lane == 0) {
-        w.steps[t] = tot;
+        w.steps[t] = (rs_q ? w.steps[t] : 0) + tot;
         atomicMax(w.maxdepth, md);
     }
 }
@@ -420,12 +462,13 @@ __global__ void __launch_bounds__(128) k_wilson_warp(GraphView g, WaveView w, ui
 }  // namespace
 
 cudaError_t launch_wilson_warp(const GraphView &g, WaveView w, uint64_t seed, const int64_t *sids,
-                               const int32_t *sorder, int64_t step_cap, cudaStream_t s) {
+                               const int32_t *sorder, int64_t step_cap, cudaStream_t s,
+                               const int32_t *rs_q, const int32_t *rs_pos) {
     // a correct run needs at most about 3 iterations per departure (walk,
     // count, commit / pop), however the walkers serialise
     const int64_t iter_cap = 4 * step_cap + 64 * g.n + 4096;
-    k_wilson_warp<<<(unsigned)((w.B * 32 + 127) / 128), 128, 0, s>>>(g, w, seed, sids, sorder,
-                                                                      step_cap, iter_cap);
+    k_wilson_warp<<<(unsigned)((w.B * 32 + 127) / 128), 128, 0, s>>>(
+        g, w, seed, sids, sorder, step_cap, iter_cap, rs_q, rs_pos);
     return cudaGetLastError();
 }
 
@@ -437,8 +480,10 @@ cudaError_t launch_wave_init(const GraphView &g, WaveView w, cudaStream_t s) {
 }
 
 cudaError_t launch_wilson(const GraphView &g, WaveView w, uint64_t seed, const int64_t *sids,
-                          int64_t step_cap, cudaStream_t s) {
-    k_wilson<<<(unsigned)((w.B + 127) / 128), 128, 0, s>>>(g, w, seed, sids, step_cap);
+                          int64_t step_cap, cudaStream_t s, const int32_t *sorder, int32_t *rs_q,
+                          int32_t *rs_pos, unsigned int *done, int64_t q_stop, int64_t stop_at) {
+    k_wilson<<<(unsigned)((w.B + 127) / 128), 128, 0, s>>>(g, w, seed, sids, sorder, step_cap,
+                                                           rs_q, rs_pos, done, q_stop, stop_at);
     return cudaGetLastError();
 }
 

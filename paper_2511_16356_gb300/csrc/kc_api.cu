@@ -102,6 +102,7 @@ size_t ws_size(const kc_graph *g, const Plan &p) {
     b += align256(sizeof(uint64_t) * n * p.BW);      // word
     b += align256(sizeof(int32_t) * n * p.BW);       // ord
     b += 3 * align256(sizeof(int64_t) * p.BW);       // steps, f, sids
+    b += 2 * align256(sizeof(int32_t) * p.BW) + 256;  // hybrid hand-off: rs_q, rs_pos, done
     b += align256(sizeof(int32_t) * n * p.BT);       // size
     b += align256(sizeof(int64_t) * n * p.BT);       // vol
     b += align256(sizeof(int32_t) * n * p.BT);       // din
@@ -113,6 +114,8 @@ size_t ws_size(const kc_graph *g, const Plan &p) {
 struct Carved {
     WaveView wv;       // Wilson-wave view (B = BW), traversal fields point at sub-wave buffers
     int64_t *sids;
+    int32_t *rs_q, *rs_pos;  // lane-to-warp hand-off of the hybrid walker
+    unsigned int *done;
 };
 
 Carved carve(kc_graph *g, const Plan &p) {
@@ -133,6 +136,9 @@ Carved carve(kc_graph *g, const Plan &p) {
     w.steps = (int64_t *)take(sizeof(int64_t) * p.BW);
     w.f = (int64_t *)take(sizeof(int64_t) * p.BW);
     c.sids = (int64_t *)take(sizeof(int64_t) * p.BW);
+    c.rs_q = (int32_t *)take(sizeof(int32_t) * p.BW);
+    c.rs_pos = (int32_t *)take(sizeof(int32_t) * p.BW);
+    c.done = (unsigned int *)take(256);
     w.size = (int32_t *)take(sizeof(int32_t) * n * p.BT);
     w.vol = (int64_t *)take(sizeof(int64_t) * n * p.BT);
     w.din = (int32_t *)take(sizeof(int32_t) * n * p.BT);
@@ -229,6 +235,33 @@ int64_t step_cap_of(const kc_graph *g) {
     return std::max<int64_t>((int64_t)1 << 22, 1024 * g->n);
 }
 
+// Wilson's algorithm for the B trees of `w` (words and order already
+// initialised, w.pos0 vertices placed) with the handle's walker.
+void run_wilson(kc_graph *g, const GraphView &gv, const WaveView &w, const Carved &c) {
+    const int64_t cap = step_cap_of(g);
+    if (g->walker == KC_WALK_LANE) {
+        KC_CK(g, launch_wilson(gv, w, g->seed, c.sids, cap, g->stream));
+    } else if (g->walker == KC_WALK_WARP) {
+        KC_CK(g, launch_wilson_warp(gv, w, g->seed, c.sids, g->d_sorder, cap, g->stream));
+    } else {
+        // lane walkers take the first starts of the hashed order (the long
+        // early walks, where concurrent walkers would mostly wait on each
+        // other); whatever is left, and lanes still running once most of the
+        // wave has finished, continue with 32 walkers per tree
+        const int pm = g->cfg.hybrid_prefix_permille > 0 ? g->cfg.hybrid_prefix_permille : 1000;
+        const int tm = g->cfg.hybrid_tail_permille > 0 ? g->cfg.hybrid_tail_permille : 900;
+        const int64_t q_stop = pm >= 1000 ? g->n : (g->n * pm) / 1000;
+        const int64_t stop_at = tm >= 1000 ? 0 : std::max<int64_t>(1, (w.B * tm + 999) / 1000);
+        KC_CK(g, cudaMemsetAsync(c.done, 0, sizeof(unsigned int), g->stream));
+        KC_CK(g, launch_wilson(gv, w, g->seed, c.sids, cap, g->stream, g->d_sorder, c.rs_q,
+                               c.rs_pos, c.done, q_stop, stop_at));
+        KC_CK(g, launch_wilson_warp(gv, w, g->seed, c.sids, g->d_sorder, cap, g->stream, c.rs_q,
+                                    c.rs_pos));
+    }
+}
+
+int wilson_launches(const kc_graph *g) { return g->walker == KC_WALK_HYBRID ? 2 : 1; }
+
 // One full sampling pass over sample ids [sid0, sid0 + B): walk, traverse,
 // evaluate f.  Leaves per-tree results in the carved workspace.
 void run_wave(kc_graph *g, Plan &p, int64_t B, int64_t sid0) {
@@ -245,12 +278,8 @@ void run_wave(kc_graph *g, Plan &p, int64_t B, int64_t sid0) {
     }
     {
         Phase ph(g, g->t_wilson);
-        if (g->walker == KC_WALK_LANE)
-            KC_CK(g, launch_wilson(gv, w, g->seed, c.sids, step_cap_of(g), g->stream));
-        else
-            KC_CK(g, launch_wilson_warp(gv, w, g->seed, c.sids, g->d_sorder, step_cap_of(g),
-                                        g->stream));
-        ph.done(1);
+        run_wilson(g, gv, w, c);
+        ph.done(wilson_launches(g));
     }
     uint32_t hdr[2] = {0, 0};
     KC_CK(g, cudaMemcpy(hdr, g->d_err, sizeof(hdr), cudaMemcpyDeviceToHost));
@@ -619,18 +648,14 @@ void resample_slots(kc_graph *g, const std::vector<int64_t> &slots, bool cond, i
             KC_CK(g, launch_wave_init(gv, w, g->stream));
             w.pos0 = 1;
         }
-        if (g->walker == KC_WALK_LANE)
-            KC_CK(g, launch_wilson(gv, w, g->seed, c.sids, step_cap_of(g), g->stream));
-        else
-            KC_CK(g, launch_wilson_warp(gv, w, g->seed, c.sids, g->d_sorder, step_cap_of(g),
-                                        g->stream));
+        run_wilson(g, gv, w, c);
         KC_CK(g, launch_words_to_slots(g->n, b, w.word, ub.slots, g->d_parents, g->root,
                                        cond ? v : -1, g->d_err, g->stream));
         KC_CK(g, launch_scatter_results(ub.slots, b, nullptr, w.steps, c.sids, g->d_f,
                                         g->d_steps, g->d_sid, g->stream));
         check_err(g, "resample");
         g->next_sid += b;
-        g->t_update.launches += 5;
+        g->t_update.launches += 4 + wilson_launches(g);
         std::vector<int64_t> part(slots.begin() + c0, slots.begin() + c0 + b);
         for (int64_t x : part) g->h_modified[(size_t)x] = 1;
         refresh_slots(g, part);
@@ -804,8 +829,11 @@ void do_sample(kc_graph *g, int64_t ntrees) {
     const int64_t pool0 = g->pool, sid_base = g->next_sid;
     int64_t done = 0;
     try {
+        // equal waves: a short last wave would take as long as a full one
+        const int64_t waves = (ntrees + p.BW - 1) / p.BW;
+        const int64_t per_wave = (ntrees + waves - 1) / waves;
         while (done < ntrees) {
-            const int64_t B = std::min<int64_t>(p.BW, ntrees - done);
+            const int64_t B = std::min<int64_t>(per_wave, ntrees - done);
             run_wave(g, p, B, sid_base + done);
             Carved c = carve(g, p);
             WaveView w = c.wv;
@@ -920,6 +948,9 @@ kc_status kc_graph_create(int64_t n, const int64_t *row_off, const int32_t *col,
         if (cfg_in->struct_size != sizeof(kc_config)) return KC_ERR_INVALID_ARG;
         cfg = *cfg_in;
     }
+    if (cfg.walker < KC_WALK_AUTO || cfg.walker > KC_WALK_HYBRID ||
+        cfg.hybrid_prefix_permille < 0 || cfg.hybrid_tail_permille < 0)
+        return KC_ERR_INVALID_ARG;
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
         (void)cudaGetLastError();
@@ -1048,11 +1079,13 @@ kc_status kc_graph_create(int64_t n, const int64_t *row_off, const int32_t *col,
         if (variant == KC_TTF_AUTO) variant = (g->ecc <= 2 * lg) ? KC_TTF_SCAN : KC_TTF_BIT;
         if (variant == KC_TTF_BIT && twom >= ((int64_t)1 << 31)) variant = KC_TTF_SCAN;
         g->ttf_variant = variant;
-        // Walkers: 32 per tree pay off when walks are short (low eccentricity);
-        // on long-diameter graphs the concurrent walkers mostly wait on each
-        // other and one walker per tree keeps more trees' walks in flight.
+        // Walkers: one sequential walker per tree leaves the GPU nearly idle
+        // whenever fewer trees fit in memory than it has warp slots, and a wave
+        // lasts as long as its slowest tree; 32 walkers per tree finish the
+        // long trees of road-shaped graphs about 4 steps per iteration, so they
+        // are the default on every graph.
         int walker = cfg.walker;
-        if (walker == KC_WALK_AUTO) walker = (g->ecc <= 2 * lg) ? KC_WALK_WARP : KC_WALK_LANE;
+        if (walker == KC_WALK_AUTO) walker = KC_WALK_WARP;
         g->walker = walker;
     } catch (Fail &f) {
         kc_graph_destroy(g);

@@ -255,9 +255,12 @@ cudaError_t launch_level_order(int64_t n, int32_t ecc, const int32_t *level, int
 
 cudaError_t launch_wave_init(const GraphView &g, WaveView w, cudaStream_t s);
 cudaError_t launch_wilson(const GraphView &g, WaveView w, uint64_t seed, const int64_t *sids,
-                          int64_t step_cap, cudaStream_t s);
+                          int64_t step_cap, cudaStream_t s, const int32_t *sorder = nullptr,
+                          int32_t *rs_q = nullptr, int32_t *rs_pos = nullptr,
+                          unsigned int *done = nullptr, int64_t q_stop = 0, int64_t stop_at = 0);
 cudaError_t launch_wilson_warp(const GraphView &g, WaveView w, uint64_t seed, const int64_t *sids,
-                               const int32_t *sorder, int64_t step_cap, cudaStream_t s);
+                               const int32_t *sorder, int64_t step_cap, cudaStream_t s,
+                               const int32_t *rs_q = nullptr, const int32_t *rs_pos = nullptr);
 cudaError_t launch_traverse(const GraphView &g, WaveView w, bool want_preorder, cudaStream_t s,
                             int *launches);
 cudaError_t launch_ttf_scan(const GraphView &g, WaveView w, cudaStream_t s);

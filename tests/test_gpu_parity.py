@@ -87,6 +87,36 @@ def test_trees_bit_exact(name, variant, walker):
             assert tr["f"] == ref.f and tr["steps"] == ref.steps
 
 
+@pytest.mark.parametrize("prefix,tail", [(0, 0), (1, 1000), (250, 1000), (1000, 500),
+                                         (400, 1)])
+@pytest.mark.parametrize("name", ["er300", "grid17x13", "path33", "star9", "cl3000",
+                                  "grid60x60"])
+def test_hybrid_walker_bit_exact(name, prefix, tail):
+    """Lane walkers for a prefix of the start order, or until a share of the
+    wave has finished, then 32 walkers per tree from the saved state: the same
+    trees and step counts as the sequential oracle.  prefix 1 hands every tree
+    over before its first start; tail 1 hands over all but the first tree."""
+    g = S.grid(60, 60) if name == "grid60x60" else SMALL[name]()
+    t0 = O.tau0(g)
+    seed = 77
+    ntrees = 96
+    cfg = _cfg(walker=kc.KC_WALK_HYBRID, hybrid_prefix_permille=prefix,
+               hybrid_tail_permille=tail)
+    with kc.KemenyGraph.from_graph(g, cfg) as G:
+        assert G.stats()["walker"] == kc.KC_WALK_HYBRID
+        G.sample(seed, ntrees)
+        got = G.samples()
+        f_ref, st_ref = O.sample_batch(g, t0, seed, 0, ntrees)
+        assert np.array_equal(got["steps"], st_ref)
+        assert np.array_equal(got["f"], f_ref)
+        for k in [0, ntrees - 1]:
+            tr = G.tree(k)
+            ref = O.tree(g, t0, seed, k)
+            assert np.array_equal(tr["parent"], ref.parent)
+            assert np.array_equal(tr["depth"], ref.depth)
+            assert np.array_equal(tr["din"], ref.din)
+
+
 def test_launch_shape_does_not_change_trees():
     """Trees depend on (seed, sample id) only: one tree in flight or all of them,
     and sampling in several calls, give the same pool."""
