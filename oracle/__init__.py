@@ -10,3 +10,5 @@ identities from the paper).  Nothing here is "parity unpinned".
 """
 from .core import *  # noqa: F401,F403
 from .exact import *  # noqa: F401,F403
+from .blocktri import *  # noqa: F401,F403
+from .hutchinson import *  # noqa: F401,F403

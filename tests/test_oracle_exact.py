@@ -102,3 +102,52 @@ def test_hoeffding_sample_size_matches_theorem5_shape():
     # kappa >= (n-1)^2/n holds with equality on K_n (the bound the proof needs)
     for n in [3, 6, 11]:
         assert O.K_dense(S.complete(n)) == pytest.approx((n - 1) ** 2 / n)
+
+
+@pytest.mark.parametrize("w,h,frac,seed", [(12, 9, 0.25, 1), (30, 40, 0.25, 2), (45, 44, 0.0, 0),
+                                           (7, 60, 0.3, 5)])
+def test_block_tridiagonal_equals_eigen(w, h, frac, seed):
+    """Selected inversion of the grounded grid Laplacian against the dense
+    eigendecomposition of the normalised Laplacian (Eq. 1)."""
+    g = S.grid_perturbed(w, h, frac, seed) if frac > 0 else S.grid(w, h)
+    assert O.K_block_tridiagonal(g, w) == pytest.approx(O.K_dense(g), rel=1e-10)
+
+
+def test_block_tridiagonal_path_is_tree_formula():
+    """A path numbered in order is block tridiagonal for any block width; its
+    only spanning tree is itself (closed form of Theorem 1 for trees)."""
+    g = S.path(120)
+    for w in (2, 5, 12, 40):
+        assert O.K_block_tridiagonal(g, w) == pytest.approx(O.K_tree_graph(g), rel=1e-10)
+
+
+def test_block_tridiagonal_rejects_other_layouts():
+    with pytest.raises(ValueError):
+        O.K_block_tridiagonal(S.torus(10, 10), 10)  # wrap-around rows
+    with pytest.raises(ValueError):
+        O.K_block_tridiagonal(S.grid(10, 10), 7)  # width does not divide n
+
+
+@pytest.mark.parametrize("gname", ["er300", "cl800"])
+def test_pinv_quadratic_form_matches_dense(gname):
+    """CG solve of the normalised Laplacian against the dense pseudo-inverse,
+    for Rademacher probes and for the unit vectors (whose sum is Tr N^+ = K)."""
+    g = S.er_lcc(300, 0.02, 7) if gname == "er300" else S.chung_lu(800, 2.1, 8.0, 3)
+    Nd = np.linalg.pinv(O.normalized_laplacian(g).toarray(), hermitian=True)
+    rng = np.random.default_rng(1)
+    Z = rng.integers(0, 2, size=(g.n, 5)).astype(np.float64) * 2 - 1
+    got = O.quad_pinv(g, Z, tol=1e-12)
+    want = np.einsum("ij,ij->j", Z, Nd @ Z)
+    assert np.allclose(got, want, rtol=1e-8)
+    unit = O.quad_pinv(g, np.eye(g.n), tol=1e-12)
+    assert unit.sum() == pytest.approx(O.K_dense(g), rel=1e-8)
+
+
+def test_hutchinson_mean_covers_exact_on_chung_lu():
+    """Config-0-sized Chung-Lu graph: the probe mean lies within 4 standard
+    errors of the exact K, and the standard error is small."""
+    g = S.chung_lu(2000, 2.1, 17.0, 2)
+    k = O.K_dense(g)
+    mean, se, _ = O.K_hutchinson(g, 96, seed=5)
+    assert abs(mean - k) <= 4 * se
+    assert se / k < 0.01
