@@ -219,7 +219,7 @@ enum : int {
     pIdle = 0,     // needs a start vertex
     pWalk = 1,     // owns frontier c and departs from it
     pWait = 2,     // arrow (or empty path) points at x, owned by another lane
-    pArrive = 3,   // reload frontier c (word and record) before walking
+    pArrive = 3,   // unused (the re-departure vertex's word and record are kept)
     pPopSet = 4,   // read the re-departure vertex before freeing a popped segment
     pPop = 5,      // free the vertices pcur .. pend of a popped cycle
     pCount = 6,    // length of the committed path
@@ -254,7 +254,7 @@ __global__ void __launch_bounds__(128, 7) k_wilson_warp(GraphView g, WaveView w,
     int ph = pIdle;
     bool has_path = false;
     int32_t s = -1, c = -1, x = -1, u = -1, pcur = -1, pend = -1, prew = -1;
-    uint32_t cc = 0, prew_cc = 0;
+    uint32_t cc = 0;
     VRec rc;
     rc.deg = 1;
     int32_t len = 0, i = 0, dh = 0, mypos = 0, maxd = 0;
@@ -298,8 +298,6 @@ __global__ void __launch_bounds__(128, 7) k_wilson_warp(GraphView g, WaveView w,
             ld = s;
         } else if (ph == pWait) {
             ld = x;
-        } else if (ph == pArrive) {
-            ld = c;
         } else if (ph == pPopSet) {
             ld = prew;
         } else if (ph == pPop) {
@@ -313,7 +311,7 @@ __global__ void __launch_bounds__(128, 7) k_wilson_warp(GraphView g, WaveView w,
         rl.deg = 1;
         if (ld >= 0) wl = ld_word(word + ld);
         const bool may_walk = (ph == pIdle || ph == pWalk || ph == pWait);
-        if ((may_walk || ph == pArrive) && ld >= 0) rl = rec[ld];
+        if ((may_walk || ph == pPopSet) && ld >= 0) rl = rec[ld];
         // ---- resolve
         const bool inT = w_in_tree(wl);
         const bool own = !inT && o_owned(wl);
@@ -346,9 +344,11 @@ __global__ void __launch_bounds__(128, 7) k_wilson_warp(GraphView g, WaveView w,
                     len = 0;
                 }
             } else if (ownr == lane) {
-                // loop closed on the own path: free next(ld) .. c, re-depart from ld
+                // loop closed on the own path: free next(ld) .. c, then re-depart
+                // from ld, whose departure count and record are kept meanwhile
                 prew = ld;
-                prew_cc = o_count(wl);
+                cc = o_count(wl);
+                rc = rl;
                 pcur = w_next(wl);
                 pend = c;
                 ph = pPop;
@@ -357,14 +357,10 @@ __global__ void __launch_bounds__(128, 7) k_wilson_warp(GraphView g, WaveView w,
                 x = ld;
                 ph = pWait;
             }
-        } else if (ph == pArrive) {
+        } else if (ph == pPopSet) {
             cc = o_count(wl);
             rc = rl;
-            ph = pWalk;
-        } else if (ph == pPopSet) {
-            prew_cc = o_count(wl);
             if (prew == c) {
-                cc = prew_cc;  // c's record is still in rc
                 ph = pWalk;
             } else {
                 pcur = w_next(wl);
@@ -376,7 +372,7 @@ __global__ void __launch_bounds__(128, 7) k_wilson_warp(GraphView g, WaveView w,
             st_word(word + pcur, o_free(nx, o_count(wl)));
             if (pcur == pend) {
                 c = prew;
-                ph = pArrive;
+                ph = pWalk;
             } else {
                 pcur = nx;
                 if (pcur < 0 || pcur >= n) bad = true;
