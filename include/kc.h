@@ -119,7 +119,7 @@ typedef struct {
     int64_t batch_trees;        /* kc_estimate batch size (0: 1024)                 */
     int64_t max_trees;          /* kc_estimate cap on the pool size (0: 1 << 24)     */
     int64_t step_cap;           /* per-tree cap on Wilson steps (0: max(2^22, 1024 n)) */
-    double mem_fraction;        /* share of free device memory for workspaces (0: 0.6) */
+    double mem_fraction;        /* share of free device memory for workspaces (0: 0.8) */
     int64_t sample_id_base;     /* first sample id of the pool (0); ranks of a
                                    multi-GPU run use disjoint bases, ids < 2^32   */
     int32_t hybrid_prefix_permille; /* KC_WALK_HYBRID: starts of the lane phase, in

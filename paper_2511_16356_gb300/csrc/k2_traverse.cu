@@ -15,7 +15,11 @@
 //   (c) top-down, over the parent-first order: in[v] = in[p] + 1 + offset(v),
 //       chains inside the chunk resolved by pointer jumping (5 rounds).
 // The resulting DFN is the preorder from 0 that visits children in ascending id;
-// out[v] = in[v] + size[v] - 1.
+// out[v] = in[v] + size[v] - 1.  Where any valid DFN serves (f of Theorem 3
+// needs only the ancestor test in[x] <= in[v] <= out[x]), (a) and (b) are
+// replaced by one leaf-to-root pass of atomic reports (below).
+#include <algorithm>
+
 #include "kc_common.cuh"
 
 namespace kc {
@@ -74,6 +78,161 @@ __global__ void __launch_bounds__(128) k_bottom_up(GraphView g, WaveView w) {
     }
 }
 
+// Where any valid DFN will do, subtree sizes, volumes and sibling offsets come
+// from one fully parallel pass instead of the chunked (a) + (b): every leaf
+// starts a thread that reports its totals to its parent with atomic adds and
+// decrements the parent's count of unreported children; the thread that
+// reports last continues with the parent's totals.  A child's offset is the
+// value its atomic add to the parent's size returns (siblings are ordered as
+// they report; the order may differ between runs, the DFN stays valid and f,
+// sizes and volumes do not change).  The count of unreported children lives in
+// the high half of the walker word, whose departure count / depth is no longer
+// needed once the tree is complete.  din marks leaves before the pass (-1; -2
+// for a vertex with children) and holds the offsets after it, so a vertex whose
+// count drops to zero during the pass is never mistaken for a leaf.
+__device__ __forceinline__ uint32_t *pending_of(uint64_t *word, int64_t v) {
+    return reinterpret_cast<uint32_t *>(word + v) + 1;
+}
+__device__ __forceinline__ int32_t parent_of(const uint64_t *word, int64_t v) {
+    return *reinterpret_cast<const int32_t *>(word + v);  // low half only
+}
+
+__global__ void k_tree_prep(GraphView g, WaveView w) {
+    const int64_t n = g.n;
+    const int64_t t = blockIdx.y;
+    uint64_t *word = w.word + t * n;
+    int32_t *size = w.size + t * n;
+    int64_t *vol = w.vol + t * n;
+    int32_t *din = w.din + t * n;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+         v += (int64_t)gridDim.x * blockDim.x) {
+        *pending_of(word, v) = 0u;
+        size[v] = 0;
+        vol[v] = 0;
+        din[v] = -1;
+    }
+}
+
+__global__ void k_child_count(GraphView g, WaveView w) {
+    const int64_t n = g.n;
+    const int64_t t = blockIdx.y;
+    uint64_t *word = w.word + t * n;
+    int32_t *din = w.din + t * n;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+         v += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t par = parent_of(word, v);
+        if (par >= 0 && par < n) {
+            atomicAdd(pending_of(word, par), 1u);
+            din[par] = -2;
+        }
+    }
+}
+
+__global__ void k_leaf_up(GraphView g, WaveView w) {
+    const int64_t n = g.n;
+    const int64_t t = blockIdx.y;
+    uint64_t *word = w.word + t * n;
+    int32_t *size = w.size + t * n;
+    int64_t *vol = w.vol + t * n;
+    int32_t *din = w.din + t * n;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+         v += (int64_t)gridDim.x * blockDim.x) {
+        if (din[v] != -1) continue;  // has children: finished by its last child's thread
+        int32_t x = (int32_t)v;
+        int32_t sx = 1;
+        int64_t vx = (int64_t)g.deg[v];
+        int64_t hop = 0;
+        for (;; ++hop) {
+            if (hop > n) {  // longer than any root path: corrupt parent array
+                atomicOr(w.err, kErrBadTree);
+                break;
+            }
+            size[x] = sx;
+            vol[x] = vx;
+            const int32_t p = parent_of(word, x);
+            if (p < 0 || p >= n) {
+                din[x] = 0;
+                if (p >= n) atomicOr(w.err, kErrBadTree);
+                break;
+            }
+            din[x] = atomicAdd(size + p, sx);
+            atomicAdd((unsigned long long *)(vol + p), (unsigned long long)vx);
+            __threadfence();
+            if (atomicSub(pending_of(word, p), 1u) != 1u) break;
+            __threadfence();
+            sx = 1 + *(volatile int32_t *)(size + p);
+            vx = (int64_t)g.deg[p] + *(volatile long long *)(vol + p);
+            x = p;
+        }
+    }
+}
+
+// Chunked alternative to the leaf-to-root pass (better for deep trees and small
+// graphs): bottom-up over the parent-first order in reverse as in (a), with
+// children numbered as they report to their parent -- reverse order, then lane
+// order inside a chunk.  A child's offset is what an atomic add of its
+// group's sizes to the parent's size returns (parent in a later chunk), or the
+// parent's size at the chunk start plus the in-chunk siblings at lower lanes.
+__global__ void __launch_bounds__(128) k_bottom_up_offsets(GraphView g, WaveView w) {
+    const int lane = threadIdx.x & 31;
+    const int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (t >= w.B) return;
+    const int64_t n = g.n;
+    const int32_t *__restrict__ ord = w.ord + t * n;
+    const uint64_t *__restrict__ word = w.word + t * n;
+    int32_t *size = w.size + t * n;
+    int64_t *vol = w.vol + t * n;
+    int32_t *din = w.din + t * n;
+    for (int64_t base = n - 1; base >= 0; base -= 32) {
+        const int64_t p = base - lane;
+        const bool act = p >= 0;
+        int32_t v = -1, par = -2, s0 = 0, s_own = 0;
+        int64_t v_own = 0;
+        if (act) {
+            v = ord[p];
+            par = w_next(word[v]);
+            s0 = ld_cg(size + v);
+            s_own = 1 + s0;
+            v_own = (int64_t)g.deg[v] + ld_cg(vol + v);
+        }
+        int plane = -1;
+#pragma unroll 4
+        for (int j = 0; j < 32; ++j) {
+            const int32_t vj = __shfl_sync(kFull, v, j);
+            const int32_t pj = __shfl_sync(kFull, par, j);
+            const int32_t sj = __shfl_sync(kFull, s_own, j);
+            const int64_t volj = __shfl_sync(kFull, v_own, j);
+            if (act && j < lane && pj == v) { s_own += sj; v_own += volj; }
+            if (act && j > lane && vj == par) plane = j;
+        }
+        const unsigned grp = __match_any_sync(kFull, act ? par : -3 - lane);
+        int32_t excl = 0, tot = 0;
+#pragma unroll 8
+        for (int j = 0; j < 32; ++j) {
+            const int32_t sj = __shfl_sync(kFull, s_own, j);
+            if ((grp >> j) & 1u) {
+                tot += sj;
+                if (j < lane) excl += sj;
+            }
+        }
+        const int leader = __ffs(grp) - 1;
+        const bool out_parent = act && par >= 0 && plane < 0;
+        int32_t b = 0;
+        if (out_parent && lane == leader) b = atomicAdd(size + par, tot);
+        b = __shfl_sync(kFull, b, leader);
+        const int32_t ps0 = __shfl_sync(kFull, s0, plane >= 0 ? plane : lane);
+        if (act) {
+            __stcg(size + v, s_own);
+            __stcg((long long *)(vol + v), (long long)v_own);
+            if (out_parent)
+                atomicAdd((unsigned long long *)(vol + par), (unsigned long long)v_own);
+            din[v] = par < 0 ? 0 : (plane >= 0 ? ps0 : b) + excl;
+        }
+        __threadfence_block();
+        __syncwarp();
+    }
+}
+
 __global__ void __launch_bounds__(128) k_sibling_offsets(GraphView g, WaveView w) {
     const int lane = threadIdx.x & 31;
     const int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -117,15 +276,25 @@ __global__ void __launch_bounds__(128) k_top_down(GraphView g, WaveView w, int w
     const uint64_t *__restrict__ word = w.word + t * n;
     int32_t *din = w.din + t * n;
     int32_t *pre = w.aux + t * n;
+    // software pipeline: the order two chunks ahead and the parent and offset
+    // one chunk ahead are read-only here (offsets of later chunks are not
+    // overwritten before their chunk), so only in[parent] waits on the chunk
+    int32_t v = -1, par = -1, off = 0;
+    if (lane < n) {
+        v = ord[lane];
+        par = w_next(word[v]);
+        off = ld_cg(din + v);
+    }
+    int32_t v2 = (32 + lane < n) ? ord[32 + lane] : -1;
     for (int64_t base = 0; base < n; base += 32) {
-        const int64_t p = base + lane;
-        const bool act = p < n;
-        int32_t v = -1, par = -1, off = 0;
-        if (act) {
-            v = ord[p];
-            par = w_next(word[v]);
-            off = ld_cg(din + v);
+        const bool act = base + lane < n;
+        // issue the next chunk's loads
+        int32_t vn = v2, parn = -1, offn = 0;
+        if (vn >= 0) {
+            parn = w_next(word[vn]);
+            offn = ld_cg(din + vn);
         }
+        v2 = (base + 64 + lane < n) ? ord[base + 64 + lane] : -1;
         int ptr = -1;
 #pragma unroll 8
         for (int j = 0; j < 32; ++j) {
@@ -153,23 +322,39 @@ __global__ void __launch_bounds__(128) k_top_down(GraphView g, WaveView w, int w
         }
         __threadfence_block();
         __syncwarp();
+        v = vn;
+        par = parn;
+        off = offn;
     }
 }
 
 }  // namespace
 
 cudaError_t launch_traverse(const GraphView &g, WaveView w, bool want_preorder, cudaStream_t s,
-                            int *launches) {
+                            int *launches, int mode) {
     const size_t per = (size_t)(w.B * g.n);
     cudaError_t e;
-    if ((e = cudaMemsetAsync(w.size, 0, sizeof(int32_t) * per, s)) != cudaSuccess) return e;
-    if ((e = cudaMemsetAsync(w.vol, 0, sizeof(int64_t) * per, s)) != cudaSuccess) return e;
-    if ((e = cudaMemsetAsync(w.aux, 0, sizeof(int32_t) * per, s)) != cudaSuccess) return e;
     const unsigned blocks = (unsigned)((w.B * 32 + 127) / 128);
-    k_bottom_up<<<blocks, 128, 0, s>>>(g, w);
-    k_sibling_offsets<<<blocks, 128, 0, s>>>(g, w);
+    const bool canonical = mode == kTravCanonical;
+    if (mode == kTravChunked) {
+        if ((e = cudaMemsetAsync(w.size, 0, sizeof(int32_t) * per, s)) != cudaSuccess) return e;
+        if ((e = cudaMemsetAsync(w.vol, 0, sizeof(int64_t) * per, s)) != cudaSuccess) return e;
+        k_bottom_up_offsets<<<blocks, 128, 0, s>>>(g, w);
+    } else if (canonical) {
+        if ((e = cudaMemsetAsync(w.size, 0, sizeof(int32_t) * per, s)) != cudaSuccess) return e;
+        if ((e = cudaMemsetAsync(w.vol, 0, sizeof(int64_t) * per, s)) != cudaSuccess) return e;
+        // children in ascending id (the DFN the oracle and the update kernels use)
+        if ((e = cudaMemsetAsync(w.aux, 0, sizeof(int32_t) * per, s)) != cudaSuccess) return e;
+        k_bottom_up<<<blocks, 128, 0, s>>>(g, w);
+        k_sibling_offsets<<<blocks, 128, 0, s>>>(g, w);
+    } else {
+        const dim3 grid((unsigned)std::min<int64_t>((g.n + 255) / 256, 1024), (unsigned)w.B);
+        k_tree_prep<<<grid, 256, 0, s>>>(g, w);
+        k_child_count<<<grid, 256, 0, s>>>(g, w);
+        k_leaf_up<<<grid, 256, 0, s>>>(g, w);
+    }
     k_top_down<<<blocks, 128, 0, s>>>(g, w, want_preorder ? 1 : 0);
-    if (launches) *launches += 3;
+    if (launches) *launches += canonical ? 3 : (mode == kTravChunked ? 2 : 4);
     return cudaGetLastError();
 }
 

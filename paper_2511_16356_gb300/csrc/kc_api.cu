@@ -92,6 +92,7 @@ struct Plan {
     int64_t BT = 0;        // trees per traversal sub-wave
     bool bit = false;
     int64_t stack_cap = 0; // BIT stack entries per tree
+    bool canon = true;     // sub-wave buffers for the id-ordered DFN (aux array)
 };
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
@@ -106,7 +107,7 @@ size_t ws_size(const kc_graph *g, const Plan &p) {
     b += align256(sizeof(int32_t) * n * p.BT);       // size
     b += align256(sizeof(int64_t) * n * p.BT);       // vol
     b += align256(sizeof(int32_t) * n * p.BT);       // din
-    b += align256(sizeof(int32_t) * n * p.BT);       // aux
+    if (p.bit || p.canon) b += align256(sizeof(int32_t) * n * p.BT);  // aux
     if (p.bit) b += align256(sizeof(int64_t) * (n + 1) * p.BT);  // bit
     return b;
 }
@@ -142,7 +143,7 @@ Carved carve(kc_graph *g, const Plan &p) {
     w.size = (int32_t *)take(sizeof(int32_t) * n * p.BT);
     w.vol = (int64_t *)take(sizeof(int64_t) * n * p.BT);
     w.din = (int32_t *)take(sizeof(int32_t) * n * p.BT);
-    w.aux = (int32_t *)take(sizeof(int32_t) * n * p.BT);
+    w.aux = (p.bit || p.canon) ? (int32_t *)take(sizeof(int32_t) * n * p.BT) : nullptr;
     w.bit = nullptr;
     w.stack = nullptr;
     w.stack_cap = p.stack_cap;
@@ -190,21 +191,37 @@ void ensure_pool(kc_graph *g, int64_t need) {
     g->h_modified.resize((size_t)cap, 0);
 }
 
-Plan plan_for(kc_graph *g, int64_t ntrees) {
+// Trees per Wilson wave (BW: walker words and parent-first order, 12 bytes a
+// vertex) and per traversal sub-wave (BT: sizes, volumes, DFN, and for BIT the
+// preorder and the BIT itself).  Low-eccentricity graphs (SCAN) spend more time
+// in the traversal than in Wilson, so both get the same count; long-diameter
+// graphs (BIT) spend most of it in Wilson, which gets 70% of the budget.
+Plan plan_for(kc_graph *g, int64_t ntrees, bool canon = true) {
     Plan p;
     p.bit = g->ttf_variant == KC_TTF_BIT;
+    p.canon = canon;
     size_t free_b = 0, total_b = 0;
     KC_CK(g, cudaMemGetInfo(&free_b, &total_b));
-    const double frac = g->cfg.mem_fraction > 0 ? g->cfg.mem_fraction : 0.6;
+    const double frac = g->cfg.mem_fraction > 0 ? g->cfg.mem_fraction : 0.8;
     const double budget = (double)(free_b + g->ws_bytes) * frac;
     const double n = (double)g->n;
-    const double per_w = 12.0 * n + 64.0;
-    const double per_t = (p.bit ? 28.0 : 20.0) * n + 64.0 + (p.bit ? 16.0 * 4096.0 : 0.0);
-    int64_t bw = (int64_t)std::floor(0.7 * budget / per_w);
-    int64_t bt = (int64_t)std::floor(0.3 * budget / per_t);
-    bw = std::max<int64_t>(1, std::min<int64_t>(bw, ntrees));
-    if (g->cfg.max_trees_in_flight > 0) bw = std::min(bw, g->cfg.max_trees_in_flight);
-    bw = std::min<int64_t>(bw, 1 << 20);
+    const double per_w = 12.0 * n + 64.0 + 8.0;
+    const double per_t = (p.bit ? 28.0 : (canon ? 20.0 : 16.0)) * n + 64.0 +
+                         (p.bit ? 16.0 * 4096.0 : 0.0);
+    int64_t bw, bt;
+    if (p.bit) {
+        bw = (int64_t)std::floor(0.7 * budget / per_w);
+        bw = std::max<int64_t>(1, std::min<int64_t>(bw, ntrees));
+        if (g->cfg.max_trees_in_flight > 0) bw = std::min(bw, g->cfg.max_trees_in_flight);
+        bw = std::min<int64_t>(bw, 1 << 20);
+        bt = (int64_t)std::floor((budget - (double)bw * per_w) / per_t);
+    } else {
+        bw = (int64_t)std::floor(budget / (per_w + per_t));
+        bw = std::max<int64_t>(1, std::min<int64_t>(bw, ntrees));
+        if (g->cfg.max_trees_in_flight > 0) bw = std::min(bw, g->cfg.max_trees_in_flight);
+        bw = std::min<int64_t>(bw, 1 << 20);
+        bt = bw;
+    }
     bt = std::max<int64_t>(1, std::min<int64_t>(bt, bw));
     bt = std::min<int64_t>(bt, 65535);
     p.BW = bw;
@@ -233,6 +250,12 @@ void ensure_stack(kc_graph *g, Plan &p, uint32_t maxdepth) {
 int64_t step_cap_of(const kc_graph *g) {
     if (g->cfg.step_cap > 0) return g->cfg.step_cap;
     return std::max<int64_t>((int64_t)1 << 22, 1024 * g->n);
+}
+
+// Traversal for f only: leaf-to-root atomics on large graphs with shallow trees
+// (low eccentricity), the chunked warp-per-tree pass otherwise.
+int fast_traversal(const kc_graph *g) {
+    return (g->ttf_variant == KC_TTF_SCAN && g->n >= (1 << 16)) ? kTravLeafUp : kTravChunked;
 }
 
 // Wilson's algorithm for the B trees of `w` (words and order already
@@ -264,7 +287,7 @@ int wilson_launches(const kc_graph *g) { return g->walker == KC_WALK_HYBRID ? 2 
 
 // One full sampling pass over sample ids [sid0, sid0 + B): walk, traverse,
 // evaluate f.  Leaves per-tree results in the carved workspace.
-void run_wave(kc_graph *g, Plan &p, int64_t B, int64_t sid0) {
+void run_wave(kc_graph *g, Plan &p, int64_t B, int64_t sid0, bool canonical = false) {
     GraphView gv = view_of(g);
     Carved c = carve(g, p);
     WaveView w = c.wv;
@@ -308,7 +331,8 @@ void run_wave(kc_graph *g, Plan &p, int64_t B, int64_t sid0) {
         {
             Phase ph(g, g->t_traverse);
             int nl = 0;
-            KC_CK(g, launch_traverse(gv, s, p.bit, g->stream, &nl));
+            KC_CK(g, launch_traverse(gv, s, p.bit, g->stream, &nl,
+                                     canonical ? kTravCanonical : fast_traversal(g)));
             ph.done(nl);
         }
         {
@@ -611,7 +635,7 @@ void refresh_slots(kc_graph *g, const std::vector<int64_t> &slots) {
             w.B = b;
         }
         int nl = 0;
-        KC_CK(g, launch_traverse(gv, w, p.bit, g->stream, &nl));
+        KC_CK(g, launch_traverse(gv, w, p.bit, g->stream, &nl, fast_traversal(g)));
         if (p.bit) KC_CK(g, launch_ttf_bit(gv, w, g->stream));
         else KC_CK(g, launch_ttf_scan(gv, w, g->stream));
         KC_CK(g, launch_scatter_results(ub.slots, b, w.f, nullptr, nullptr, g->d_f, g->d_steps,
@@ -824,7 +848,7 @@ PoolSums reduce_pool(kc_graph *g) {
 void do_sample(kc_graph *g, int64_t ntrees) {
     if (ntrees <= 0) return;
     ensure_pool(g, g->pool + ntrees);
-    Plan p = plan_for(g, ntrees);
+    Plan p = plan_for(g, ntrees, false);
     ensure_ws(g, p);
     const int64_t pool0 = g->pool, sid_base = g->next_sid;
     int64_t done = 0;
@@ -880,7 +904,7 @@ void kc_config_default(kc_config *cfg) {
     cfg->batch_trees = 1024;
     cfg->max_trees = (int64_t)1 << 24;
     cfg->step_cap = 0;
-    cfg->mem_fraction = 0.6;
+    cfg->mem_fraction = 0.8;
 }
 
 const char *kc_status_string(kc_status s) {
@@ -1281,7 +1305,7 @@ kc_status kc_get_tree(kc_graph *g, int64_t sample, int32_t *parent, int32_t *dep
         p.bit = g->ttf_variant == KC_TTF_BIT;
         p.stack_cap = p.bit ? 4096 : 0;
         ensure_ws(g, p);
-        run_wave(g, p, 1, sid);
+        run_wave(g, p, 1, sid, true);
         Carved c = carve(g, p);
         const int64_t n = g->n;
         std::vector<uint64_t> word((size_t)n);

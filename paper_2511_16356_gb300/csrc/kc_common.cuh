@@ -261,8 +261,13 @@ cudaError_t launch_wilson(const GraphView &g, WaveView w, uint64_t seed, const i
 cudaError_t launch_wilson_warp(const GraphView &g, WaveView w, uint64_t seed, const int64_t *sids,
                                const int32_t *sorder, int64_t step_cap, cudaStream_t s,
                                const int32_t *rs_q = nullptr, const int32_t *rs_pos = nullptr);
+// Traversal modes: kTravCanonical numbers children in ascending id (the DFN the
+// oracle reports and the update kernels enumerate by); the others give some
+// valid DFN (enough for f): kTravChunked (warp per tree, for deep trees and
+// small graphs) and kTravLeafUp (leaf-to-root atomics, for large shallow trees).
+enum : int { kTravCanonical = 0, kTravChunked = 1, kTravLeafUp = 2 };
 cudaError_t launch_traverse(const GraphView &g, WaveView w, bool want_preorder, cudaStream_t s,
-                            int *launches);
+                            int *launches = nullptr, int mode = kTravCanonical);
 cudaError_t launch_ttf_scan(const GraphView &g, WaveView w, cudaStream_t s);
 cudaError_t launch_ttf_bit(const GraphView &g, WaveView w, cudaStream_t s);
 cudaError_t launch_pool_append(WaveView w, int64_t first, int64_t *pool_f, double *pool_w,

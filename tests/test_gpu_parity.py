@@ -235,3 +235,22 @@ def test_grid1000_sampled_ids_bit_exact():
         assert np.array_equal(tr["parent"], ref.parent)
         assert np.array_equal(tr["din"], ref.din)
         assert np.array_equal(tr["vol"], ref.vol)
+
+
+@pytest.mark.parametrize("name", ["cl80000", "er70000"])
+def test_large_shallow_graphs_bit_exact(name):
+    """Graphs of at least 2^16 vertices with low eccentricity take the
+    leaf-to-root traversal on the sampling path: f and step counts equal to the
+    oracle's, and the tree read back (id-ordered DFN) too."""
+    g = S.chung_lu(80000, 2.1, 10.0, 6) if name == "cl80000" else S.er_lcc(70000, 6.0 / 70000, 3)
+    t0 = O.tau0(g)
+    with kc.KemenyGraph.from_graph(g, _cfg()) as G:
+        assert G.stats()["ttf_variant"] == kc.KC_TTF_SCAN
+        G.sample(21, 96)
+        got = G.samples()
+        f_ref, st_ref = O.sample_batch(g, t0, 21, 0, 96)
+        assert np.array_equal(got["steps"], st_ref)
+        assert np.array_equal(got["f"], f_ref)
+        tr = G.tree(5)
+        ref = O.tree(g, t0, 21, 5)
+        assert np.array_equal(tr["din"], ref.din) and np.array_equal(tr["vol"], ref.vol)
