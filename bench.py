@@ -184,6 +184,12 @@ def run_reference(args):
 
 WALKER_NAMES = {1: "lane", 2: "warp", 3: "hybrid"}
 
+# DRAM bytes per Wilson departure of k_wilson_warp on road-shaped grids: an ncu
+# capture (dram__bytes) of the kernel on the 300x300 perturbed grid with 1000
+# trees in flight moved 9.70 GB for 1.133e9 departures.  The full-size launch
+# is too long to capture; its traffic is this figure times its departures.
+WILSON_WARP_GRID_DRAM_BYTES_PER_STEP = 9.70e9 / 1.1334e9
+
 
 def main():
     ap = argparse.ArgumentParser()
@@ -293,6 +299,9 @@ def main():
                               kc.KC_WALK_HYBRID: "k_wilson+k_wilson_warp"}[st["walker"]],
                    "traverse": "k_bottom_up/k_sibling_offsets/k_top_down",
                    "ttf_bit": "k_ttf_bit", "ttf_scan": "k_ttf_scan"}[dom]
+    traffic = None
+    if dom == "wilson" and st["walker"] == kc.KC_WALK_WARP and args.workload.startswith("grid"):
+        traffic = WILSON_WARP_GRID_DRAM_BYTES_PER_STEP * steps_total / max(1, dom_launches)
     phase_ms = {k: round(v[0], 3) for k, v in phases.items()}
     phase_ms["wave_init"] = round(st["ms_wave_init"], 3)
     phase_ms["reduce"] = round(st["ms_reduce"], 3)
@@ -312,7 +321,9 @@ def main():
                    "trees_in_flight": st["trees_in_flight"]},
         "roofline": {"bound": "hbm", "kernel": kernel_name, "achieved": achieved, "peak": peak,
                      "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": None,
+                     "traffic": traffic,
+                     "traffic_basis": None if traffic is None else
+                     "ncu dram bytes per departure on grid300x300 (1000 trees) x departures",
                      "algorithmic_bytes_per_launch": per_launch_bytes,
                      "mean_launch_ms": per_launch_s * 1000.0},
         "phase_ms": phase_ms,
@@ -378,7 +389,7 @@ def main():
         trees = max(2 * cores, 16)
         _, el, used = oracle_baseline(g, trees, args.seed)
         if el < 10.0:
-            more = int(min(1 << 16, max(cores, trees * (15.0 - el) / max(el, 1e-3))))
+            more = int(min(1 << 22, max(cores, trees * (15.0 - el) / max(el, 1e-3))))
             more = (more + cores - 1) // cores * cores
             _, el2, used = oracle_baseline(g, more, args.seed, first=trees)
             trees, el = trees + more, el + el2
