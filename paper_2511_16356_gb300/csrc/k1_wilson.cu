@@ -231,7 +231,11 @@ enum : int {
 // index rs_q[t] of the same start order and order position rs_pos[t], adding
 // to its step count (rs_q[t] < 0: the tree is finished and the warp exits).
 // Otherwise warp t samples tree t from scratch.
-__global__ void __launch_bounds__(128, 7) k_wilson_warp(GraphView g, WaveView w, uint64_t seed,
+// One warp per block: a block frees its SM slot as soon as its own tree is
+// done (tree times vary several-fold on long-diameter graphs, and a 4-warp
+// block would hold three finished warps' registers until its slowest tree).
+constexpr int kWarpWalkerBlock = 32;
+__global__ void __launch_bounds__(kWarpWalkerBlock, 24) k_wilson_warp(GraphView g, WaveView w, uint64_t seed,
                                                      const int64_t *__restrict__ sids,
                                                      const int32_t *__restrict__ sorder,
                                                      int64_t step_cap, int64_t iter_cap,
@@ -240,8 +244,7 @@ __global__ void __launch_bounds__(128, 7) k_wilson_warp(GraphView g, WaveView w,
     const unsigned kFull = 0xFFFFFFFFu;
     const int lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
-    __shared__ int32_t xs_all[4][32];  // per warp: vertex each cycle lane's predecessor waits on
-    int32_t *xs = xs_all[threadIdx.x >> 5];
+    __shared__ int32_t xs[32];  // vertex each cycle lane's predecessor waits on
     const int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (t >= w.B) return;                   // whole warp
     if (rs_q && rs_q[t] < 0) return;        // whole warp: finished by the lane walker
@@ -275,7 +278,9 @@ __global__ void __launch_bounds__(128, 7) k_wilson_warp(GraphView g, WaveView w,
             next_start += __popc(idle);
         }
         if (__all_sync(kFull, ph == pDone)) break;
-        if (it > iter_cap || __any_sync(kFull, bad)) {
+        // a lane that met a bad state stopped itself (pDone, nothing loaded);
+        // the warp notices within 8 iterations
+        if (it > iter_cap || ((it & 7) == 0 && __any_sync(kFull, bad))) {
             if (lane == 0) atomicOr(w.err, bad ? kErrBadTree : kErrIterLimit);
             break;
         }
@@ -288,12 +293,14 @@ __global__ void __launch_bounds__(128, 7) k_wilson_warp(GraphView g, WaveView w,
             st_word(word + c, o_own(v, cc + 1, lane));
             cc += 1;
             ++steps;
+            x = v;
+            ld = v;
             if (cc >= kCountMask || steps > step_cap) {
                 atomicOr(w.err, kErrStepLimit);
                 bad = true;
+                ph = pDone;
+                ld = -1;
             }
-            x = v;
-            ld = v;
         } else if (ph == pIdle) {
             ld = s;
         } else if (ph == pWait) {
@@ -375,7 +382,10 @@ __global__ void __launch_bounds__(128, 7) k_wilson_warp(GraphView g, WaveView w,
                 ph = pWalk;
             } else {
                 pcur = nx;
-                if (pcur < 0 || pcur >= n) bad = true;
+                if (pcur < 0 || pcur >= n) {
+                    bad = true;
+                    ph = pDone;
+                }
             }
         } else if (ph == pCount) {
             if (inT) {
@@ -384,18 +394,25 @@ __global__ void __launch_bounds__(128, 7) k_wilson_warp(GraphView g, WaveView w,
             } else {
                 ++len;
                 u = w_next(wl);
-                if (len > n || u < 0 || u >= n) bad = true;
+                if (len > n || u < 0 || u >= n) {
+                    bad = true;
+                    ph = pDone;
+                }
             }
         } else if (ph == pCommit) {
             const int32_t nx = w_next(wl);
             const int32_t d = dh + len - i;
             st_word(word + u, w_make(nx, (uint32_t)d, true));
             const int64_t slot = (int64_t)mypos + len - 1 - i;
-            if (slot > 0 && slot < n) ord[slot] = u; else bad = true;
+            if (slot > 0 && slot < n) ord[slot] = u;
             if (d > maxd) maxd = d;
             ++i;
             u = nx;
             if (i == len) ph = pIdle;
+            if (slot <= 0 || slot >= n) {
+                bad = true;
+                ph = pDone;
+            }
         }
         // ---- reserve slots of the parent-first order for paths that reached the tree
         if (__any_sync(kFull, fin)) {
@@ -420,7 +437,8 @@ __global__ void __launch_bounds__(128, 7) k_wilson_warp(GraphView g, WaveView w,
         // is succ^32 of some lane (a 32-step path among 32 lanes must have entered
         // a cycle, and succ^32 permutes each cycle), found by 5 doubling rounds.
         const int succ = (was_wait && ph == pWait && has_path && own && ownr != lane) ? ownr : -1;
-        if (__popc(__ballot_sync(kFull, succ >= 0)) >= 2) {
+        // (a cycle of waits persists until popped, so every 4th iteration suffices)
+        if ((it & 3) == 0 && __popc(__ballot_sync(kFull, succ >= 0)) >= 2) {
             int z = succ;
 #pragma unroll
             for (int r = 0; r < 5; ++r) {
@@ -463,7 +481,7 @@ cudaError_t launch_wilson_warp(const GraphView &g, WaveView w, uint64_t seed, co
     // a correct run needs at most about 3 iterations per departure (walk,
     // count, commit / pop), however the walkers serialise
     const int64_t iter_cap = 4 * step_cap + 64 * g.n + 4096;
-    k_wilson_warp<<<(unsigned)((w.B * 32 + 127) / 128), 128, 0, s>>>(
+    k_wilson_warp<<<(unsigned)w.B, kWarpWalkerBlock, 0, s>>>(
         g, w, seed, sids, sorder, step_cap, iter_cap, rs_q, rs_pos);
     return cudaGetLastError();
 }
