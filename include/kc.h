@@ -159,6 +159,21 @@ kc_status kc_graph_destroy(kc_graph *g);
 kc_status kc_graph_set_stream(kc_graph *g, void *cuda_stream);
 
 /*
+ * Serving helpers (no counterpart in the paper).
+ * kc_graph_set_workspace_limit: later calls size their per-tree workspaces to
+ *   at most `bytes` of device memory (0: a share of free memory, mem_fraction).
+ * kc_graph_release_workspace: return the workspaces to the stream-ordered
+ *   allocator (on the handle's stream, without synchronising the device).
+ * kc_graph_reset: drop every sampled tree and fix `seed` and the next sample id
+ *   (< 2^32), keeping the graph and tau0 resident; the next kc_sample or
+ *   kc_estimate starts a fresh pool.
+ * Errors: INVALID_ARG (negative bytes, id out of range), CUDA.
+ */
+kc_status kc_graph_set_workspace_limit(kc_graph *g, int64_t bytes);
+kc_status kc_graph_release_workspace(kc_graph *g);
+kc_status kc_graph_reset(kc_graph *g, uint64_t seed, int64_t sample_id_base);
+
+/*
  * Draw n_trees uniform spanning trees rooted at r with sample ids
  * [pool, pool + n_trees) under `seed` (Algorithm 1 loop: wilson, subtree
  * volumes, DFS).  Appends each tree's f(tau) (int64, exact), step count and

@@ -55,6 +55,15 @@ void dfree(T *&p) {
     p = nullptr;
 }
 
+// A blocking copy ordered after the handle's stream: the legacy default stream
+// does not wait for non-blocking streams, so plain cudaMemcpy could read
+// results before the handle's kernels finish.
+cudaError_t copy_sync(kc_graph *g, void *dst, const void *src, size_t bytes, cudaMemcpyKind kind) {
+    cudaError_t e = cudaMemcpyAsync(dst, src, bytes, kind, g->stream);
+    if (e != cudaSuccess) return e;
+    return cudaStreamSynchronize(g->stream);
+}
+
 GraphView view_of(const kc_graph *g) {
     GraphView v;
     v.n = g->n;
@@ -156,13 +165,26 @@ Carved carve(kc_graph *g, const Plan &p) {
     return c;
 }
 
+// Workspaces come from the stream-ordered allocator on the handle's stream, so
+// growing or releasing one never synchronises the device (handles on other
+// streams keep running).
 void ensure_ws(kc_graph *g, const Plan &p) {
     const size_t need = ws_size(g, p);
     if (need <= g->ws_bytes) return;
-    dfree(g->d_ws);
+    if (g->d_ws) KC_CK(g, cudaFreeAsync(g->d_ws, g->stream));
+    g->d_ws = nullptr;
     g->ws_bytes = 0;
-    KC_CK(g, cudaMalloc(&g->d_ws, need));
+    KC_CK(g, cudaMallocAsync(&g->d_ws, need, g->stream));
     g->ws_bytes = need;
+}
+
+void release_ws(kc_graph *g) {
+    if (g->d_ws) KC_CK(g, cudaFreeAsync(g->d_ws, g->stream));
+    if (g->d_stack) KC_CK(g, cudaFreeAsync(g->d_stack, g->stream));
+    g->d_ws = nullptr;
+    g->d_stack = nullptr;
+    g->ws_bytes = 0;
+    g->stack_bytes = 0;
 }
 
 // Pool growth (device arrays of per-tree values, optional parent arrays)
@@ -203,7 +225,8 @@ Plan plan_for(kc_graph *g, int64_t ntrees, bool canon = true) {
     size_t free_b = 0, total_b = 0;
     KC_CK(g, cudaMemGetInfo(&free_b, &total_b));
     const double frac = g->cfg.mem_fraction > 0 ? g->cfg.mem_fraction : 0.8;
-    const double budget = (double)(free_b + g->ws_bytes) * frac;
+    const double budget = g->ws_limit > 0 ? (double)g->ws_limit
+                                          : (double)(free_b + g->ws_bytes) * frac;
     const double n = (double)g->n;
     const double per_w = 12.0 * n + 64.0 + 8.0;
     const double per_t = (p.bit ? 28.0 : (canon ? 20.0 : 16.0)) * n + 64.0 +
@@ -236,9 +259,10 @@ void ensure_stack(kc_graph *g, Plan &p, uint32_t maxdepth) {
     const int64_t need_cap = (int64_t)maxdepth + 2;
     const size_t need = sizeof(int32_t) * 4 * (size_t)need_cap * (size_t)p.BT;
     if (need > g->stack_bytes) {
-        dfree(g->d_stack);
+        if (g->d_stack) KC_CK(g, cudaFreeAsync(g->d_stack, g->stream));
+        g->d_stack = nullptr;
         g->stack_bytes = 0;
-        KC_CK(g, cudaMalloc((void **)&g->d_stack, need));
+        KC_CK(g, cudaMallocAsync((void **)&g->d_stack, need, g->stream));
         g->stack_bytes = need;
     }
     p.stack_cap = need_cap;
@@ -305,7 +329,7 @@ void run_wave(kc_graph *g, Plan &p, int64_t B, int64_t sid0, bool canonical = fa
         ph.done(wilson_launches(g));
     }
     uint32_t hdr[2] = {0, 0};
-    KC_CK(g, cudaMemcpy(hdr, g->d_err, sizeof(hdr), cudaMemcpyDeviceToHost));
+    KC_CK(g, copy_sync(g, hdr, g->d_err, sizeof(hdr), cudaMemcpyDeviceToHost));
     if (hdr[0] & kErrStepLimit) {
         g->last_error = "Wilson walk exceeded the step cap";
         throw Fail{KC_ERR_STEP_LIMIT};
@@ -342,7 +366,7 @@ void run_wave(kc_graph *g, Plan &p, int64_t B, int64_t sid0, bool canonical = fa
             ph.done(1);
         }
     }
-    KC_CK(g, cudaMemcpy(hdr, g->d_err, sizeof(hdr), cudaMemcpyDeviceToHost));
+    KC_CK(g, copy_sync(g, hdr, g->d_err, sizeof(hdr), cudaMemcpyDeviceToHost));
     if (hdr[0] & kErrBadTree) {
         g->last_error = "inconsistent tree state or traversal stack overflow";
         throw Fail{KC_ERR_CUDA};
@@ -390,7 +414,7 @@ unsigned long long argmax_dev(kc_graph *g, const int32_t *la, const int32_t *lb,
 // highest-degree vertices, smallest id among equals.  Unique maximum: r0.
 int32_t central_root(kc_graph *g, int32_t r0, int &launches) {
     int32_t dmax = 0;
-    KC_CK(g, cudaMemcpy(&dmax, g->d_deg + r0, sizeof(int32_t), cudaMemcpyDeviceToHost));
+    KC_CK(g, copy_sync(g, &dmax, g->d_deg + r0, sizeof(int32_t), cudaMemcpyDeviceToHost));
     int32_t *d_ties = (int32_t *)g->d_scratch + 32;
     unsigned long long *d_best = (unsigned long long *)g->d_scratch + 24;
     KC_CK(g, cudaMemsetAsync(d_ties, 0, sizeof(int32_t), g->stream));
@@ -596,7 +620,7 @@ UpdBuf upd_buf(kc_graph *g) {
 
 void check_err(kc_graph *g, const char *what) {
     uint32_t hdr[2] = {0, 0};
-    KC_CK(g, cudaMemcpy(hdr, g->d_err, sizeof(hdr), cudaMemcpyDeviceToHost));
+    KC_CK(g, copy_sync(g, hdr, g->d_err, sizeof(hdr), cudaMemcpyDeviceToHost));
     if (hdr[0] & kErrStepLimit) {
         g->last_error = std::string(what) + ": Wilson walk exceeded the step cap";
         throw Fail{KC_ERR_STEP_LIMIT};
@@ -841,7 +865,7 @@ PoolSums reduce_pool(kc_graph *g) {
     Phase ph(g, g->t_reduce);
     KC_CK(g, launch_pool_reduce(g->d_f, g->d_w, g->pool, 2 * g->m, g->d_scratch, g->stream));
     ph.done(1);
-    KC_CK(g, cudaMemcpy(&s, g->d_scratch, sizeof(s), cudaMemcpyDeviceToHost));
+    KC_CK(g, copy_sync(g, &s, g->d_scratch, sizeof(s), cudaMemcpyDeviceToHost));
     return s;
 }
 
@@ -1000,7 +1024,7 @@ kc_status kc_graph_create(int64_t n, const int64_t *row_off, const int32_t *col,
         // host copy of the CSR (validated layout, kept for updates)
         g->h_row_off.resize((size_t)n + 1);
         const cudaMemcpyKind kind = cfg.inputs_on_device ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost;
-        KC_CK(g, cudaMemcpy(g->h_row_off.data(), row_off, sizeof(int64_t) * (n + 1), kind));
+        KC_CK(g, copy_sync(g, g->h_row_off.data(), row_off, sizeof(int64_t) * (n + 1), kind));
         if (g->h_row_off[0] != 0) throw Fail{KC_ERR_INVALID_ARG};
         for (int64_t v = 0; v < n; ++v)
             if (g->h_row_off[v + 1] < g->h_row_off[v]) throw Fail{KC_ERR_INVALID_ARG};
@@ -1008,7 +1032,7 @@ kc_status kc_graph_create(int64_t n, const int64_t *row_off, const int32_t *col,
         if (twom % 2 != 0 || twom == 0) throw Fail{twom == 0 ? KC_ERR_DISCONNECTED : KC_ERR_NOT_SYMMETRIC};
         g->m = twom / 2;
         g->h_col.resize((size_t)twom);
-        KC_CK(g, cudaMemcpy(g->h_col.data(), col, sizeof(int32_t) * twom, kind));
+        KC_CK(g, copy_sync(g, g->h_col.data(), col, sizeof(int32_t) * twom, kind));
 
         dalloc(g, &g->d_row_off, n + 1);
         dalloc(g, &g->d_col, twom);
@@ -1116,6 +1140,33 @@ kc_status kc_graph_create(int64_t n, const int64_t *row_off, const int32_t *col,
         return f.st;
     }
     *out = g;
+    return KC_OK;
+}
+
+kc_status kc_graph_set_workspace_limit(kc_graph *g, int64_t bytes) {
+    if (!g || bytes < 0) return KC_ERR_INVALID_ARG;
+    g->ws_limit = bytes;
+    return KC_OK;
+}
+
+kc_status kc_graph_release_workspace(kc_graph *g) {
+    if (!g) return KC_ERR_INVALID_ARG;
+    try {
+        release_ws(g);
+    } catch (Fail &f) {
+        return f.st;
+    }
+    return KC_OK;
+}
+
+kc_status kc_graph_reset(kc_graph *g, uint64_t seed, int64_t sample_id_base) {
+    if (!g || sample_id_base < 0 || sample_id_base >= ((int64_t)1 << 32))
+        return KC_ERR_INVALID_ARG;
+    g->pool = 0;
+    g->next_sid = sample_id_base;
+    g->seed = seed;
+    g->seeded = true;
+    g->last_wave = 0;
     return KC_OK;
 }
 
@@ -1278,12 +1329,12 @@ kc_status kc_get_tree(kc_graph *g, int64_t sample, int32_t *parent, int32_t *dep
             check_err(g, "get_tree");
             std::vector<uint64_t> word((size_t)n);
             std::vector<int32_t> din((size_t)n), size((size_t)n);
-            KC_CK(g, cudaMemcpy(word.data(), w.word, sizeof(uint64_t) * n, cudaMemcpyDeviceToHost));
-            KC_CK(g, cudaMemcpy(din.data(), w.din, sizeof(int32_t) * n, cudaMemcpyDeviceToHost));
-            KC_CK(g, cudaMemcpy(size.data(), w.size, sizeof(int32_t) * n, cudaMemcpyDeviceToHost));
-            if (vol) KC_CK(g, cudaMemcpy(vol, w.vol, sizeof(int64_t) * n, cudaMemcpyDeviceToHost));
-            if (f) KC_CK(g, cudaMemcpy(f, g->d_f + sample, sizeof(int64_t), cudaMemcpyDeviceToHost));
-            if (steps) KC_CK(g, cudaMemcpy(steps, g->d_steps + sample, sizeof(int64_t),
+            KC_CK(g, copy_sync(g, word.data(), w.word, sizeof(uint64_t) * n, cudaMemcpyDeviceToHost));
+            KC_CK(g, copy_sync(g, din.data(), w.din, sizeof(int32_t) * n, cudaMemcpyDeviceToHost));
+            KC_CK(g, copy_sync(g, size.data(), w.size, sizeof(int32_t) * n, cudaMemcpyDeviceToHost));
+            if (vol) KC_CK(g, copy_sync(g, vol, w.vol, sizeof(int64_t) * n, cudaMemcpyDeviceToHost));
+            if (f) KC_CK(g, copy_sync(g, f, g->d_f + sample, sizeof(int64_t), cudaMemcpyDeviceToHost));
+            if (steps) KC_CK(g, copy_sync(g, steps, g->d_steps + sample, sizeof(int64_t),
                                            cudaMemcpyDeviceToHost));
             for (int64_t v = 0; v < n; ++v) {
                 if (parent) parent[v] = w_next(word[(size_t)v]);
@@ -1298,7 +1349,7 @@ kc_status kc_get_tree(kc_graph *g, int64_t sample, int32_t *parent, int32_t *dep
     }
     try {
         int64_t sid = 0;
-        KC_CK(g, cudaMemcpy(&sid, g->d_sid + sample, sizeof(int64_t), cudaMemcpyDeviceToHost));
+        KC_CK(g, copy_sync(g, &sid, g->d_sid + sample, sizeof(int64_t), cudaMemcpyDeviceToHost));
         Plan p;
         p.BW = 1;
         p.BT = 1;
@@ -1310,12 +1361,12 @@ kc_status kc_get_tree(kc_graph *g, int64_t sample, int32_t *parent, int32_t *dep
         const int64_t n = g->n;
         std::vector<uint64_t> word((size_t)n);
         std::vector<int32_t> din((size_t)n), size((size_t)n);
-        KC_CK(g, cudaMemcpy(word.data(), c.wv.word, sizeof(uint64_t) * n, cudaMemcpyDeviceToHost));
-        KC_CK(g, cudaMemcpy(din.data(), c.wv.din, sizeof(int32_t) * n, cudaMemcpyDeviceToHost));
-        KC_CK(g, cudaMemcpy(size.data(), c.wv.size, sizeof(int32_t) * n, cudaMemcpyDeviceToHost));
-        if (vol) KC_CK(g, cudaMemcpy(vol, c.wv.vol, sizeof(int64_t) * n, cudaMemcpyDeviceToHost));
-        if (f) KC_CK(g, cudaMemcpy(f, c.wv.f, sizeof(int64_t), cudaMemcpyDeviceToHost));
-        if (steps) KC_CK(g, cudaMemcpy(steps, c.wv.steps, sizeof(int64_t), cudaMemcpyDeviceToHost));
+        KC_CK(g, copy_sync(g, word.data(), c.wv.word, sizeof(uint64_t) * n, cudaMemcpyDeviceToHost));
+        KC_CK(g, copy_sync(g, din.data(), c.wv.din, sizeof(int32_t) * n, cudaMemcpyDeviceToHost));
+        KC_CK(g, copy_sync(g, size.data(), c.wv.size, sizeof(int32_t) * n, cudaMemcpyDeviceToHost));
+        if (vol) KC_CK(g, copy_sync(g, vol, c.wv.vol, sizeof(int64_t) * n, cudaMemcpyDeviceToHost));
+        if (f) KC_CK(g, copy_sync(g, f, c.wv.f, sizeof(int64_t), cudaMemcpyDeviceToHost));
+        if (steps) KC_CK(g, copy_sync(g, steps, c.wv.steps, sizeof(int64_t), cudaMemcpyDeviceToHost));
         for (int64_t v = 0; v < n; ++v) {
             if (parent) parent[v] = w_next(word[(size_t)v]);
             if (depth) depth[v] = (int32_t)w_count(word[(size_t)v]);
@@ -1364,14 +1415,14 @@ kc_status kc_stats(kc_graph *g, kc_stats_t *out) {
     if (g->pool > 0) {
         try {
             std::vector<int64_t> st((size_t)g->pool);
-            KC_CK(g, cudaMemcpy(st.data(), g->d_steps, sizeof(int64_t) * g->pool,
+            KC_CK(g, copy_sync(g, st.data(), g->d_steps, sizeof(int64_t) * g->pool,
                                 cudaMemcpyDeviceToHost));
             int64_t tot = 0;
             for (int64_t x : st) tot += x;
             out->total_steps = tot;
             PoolSums s{};
             KC_CK(g, launch_pool_reduce(g->d_f, g->d_w, g->pool, 2 * g->m, g->d_scratch, g->stream));
-            KC_CK(g, cudaMemcpy(&s, g->d_scratch, sizeof(s), cudaMemcpyDeviceToHost));
+            KC_CK(g, copy_sync(g, &s, g->d_scratch, sizeof(s), cudaMemcpyDeviceToHost));
             out->f_sum_hi = s.f_hi;
             out->f_sum_lo = s.f_lo;
             out->wf_sum = s.wf;

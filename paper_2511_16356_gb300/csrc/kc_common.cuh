@@ -202,6 +202,7 @@ struct kc_graph {
     uint64_t seed = 0;
     int64_t pool = 0, pool_cap = 0;
     int64_t next_sid = 0;
+    int64_t ws_limit = 0;  // workspace byte budget (0: a share of free memory)
     int64_t *d_f = nullptr;
     double *d_w = nullptr;
     int64_t *d_steps = nullptr;

@@ -78,7 +78,24 @@ class kc_stats_t(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in _STATS_FIELDS}
 
 
-# The C prototypes, in header order.
+class kc_server_config(ctypes.Structure):
+    _fields_ = [("struct_size", ctypes.c_uint32), ("workers", ctypes.c_int32),
+                ("budget_bytes", ctypes.c_int64), ("request_bytes", ctypes.c_int64)]
+
+
+class kc_request_info(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("kind", ctypes.c_int32), ("graph", ctypes.c_int32),
+                ("worker", ctypes.c_int32), ("K", ctypes.c_double), ("trees", ctypes.c_int64),
+                ("t_submit_ms", ctypes.c_double), ("t_start_ms", ctypes.c_double),
+                ("t_end_ms", ctypes.c_double), ("workspace_bytes", ctypes.c_int64)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+KC_REQ_QUERY, KC_REQ_POOL_QUERY, KC_REQ_UPDATE = 0, 1, 2
+
+# The C prototypes, in header order (kc.h, then kc_serve.h).
 _P = ctypes.c_void_p
 _SIGS = {
     "kc_config_default": (None, [ctypes.POINTER(kc_config)]),
@@ -86,6 +103,9 @@ _SIGS = {
                                        ctypes.POINTER(_P)]),
     "kc_graph_destroy": (ctypes.c_int, [_P]),
     "kc_graph_set_stream": (ctypes.c_int, [_P, _P]),
+    "kc_graph_set_workspace_limit": (ctypes.c_int, [_P, ctypes.c_int64]),
+    "kc_graph_release_workspace": (ctypes.c_int, [_P]),
+    "kc_graph_reset": (ctypes.c_int, [_P, ctypes.c_uint64, ctypes.c_int64]),
     "kc_sample": (ctypes.c_int, [_P, ctypes.c_uint64, ctypes.c_int64]),
     "kc_estimate": (ctypes.c_int, [_P, ctypes.c_double, ctypes.c_double,
                                    ctypes.POINTER(ctypes.c_double)]),
@@ -100,6 +120,25 @@ _SIGS = {
     "kc_reset_timers": (ctypes.c_int, [_P]),
     "kc_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "kc_last_error": (ctypes.c_char_p, [_P]),
+    "kc_server_config_default": (None, [ctypes.POINTER(kc_server_config)]),
+    "kc_server_create": (ctypes.c_int, [ctypes.POINTER(kc_server_config), ctypes.POINTER(_P)]),
+    "kc_server_destroy": (ctypes.c_int, [_P]),
+    "kc_server_add_graph": (ctypes.c_int, [_P, ctypes.c_int64, _P, _P, ctypes.POINTER(kc_config),
+                                           ctypes.c_uint64, ctypes.c_int64,
+                                           ctypes.POINTER(ctypes.c_int32)]),
+    "kc_server_submit_query": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_uint64,
+                                              ctypes.c_double, ctypes.c_double,
+                                              ctypes.POINTER(ctypes.c_int64)]),
+    "kc_server_submit_pool_query": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_double,
+                                                   ctypes.c_double,
+                                                   ctypes.POINTER(ctypes.c_int64)]),
+    "kc_server_submit_update": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(kc_edge_op),
+                                               ctypes.c_int64, ctypes.c_int32,
+                                               ctypes.POINTER(ctypes.c_int64)]),
+    "kc_server_wait": (ctypes.c_int, [_P, ctypes.c_int64, ctypes.POINTER(kc_request_info)]),
+    "kc_server_poll": (ctypes.c_int, [_P, ctypes.c_int64, ctypes.POINTER(ctypes.c_int32),
+                                      ctypes.POINTER(kc_request_info)]),
+    "kc_server_drain": (ctypes.c_int, [_P]),
 }
 EXPORTED = tuple(_SIGS)
 
@@ -289,6 +328,87 @@ class KemenyGraph:
     def close(self):
         if getattr(self, "h", None):
             kc_graph_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+def _edge_ops(ops):
+    ops = list(ops)
+    arr = (kc_edge_op * max(1, len(ops)))()
+    for i, o in enumerate(ops):
+        arr[i].u, arr[i].v, arr[i].op = int(o[0]), int(o[1]), int(o[2])
+        arr[i].r = float(o[3]) if len(o) > 3 else 0.0
+    return arr, len(ops)
+
+
+class Server:
+    """Owning wrapper around a kc_server (resident graphs, continuous batching)."""
+
+    def __init__(self, workers: int = 4, budget_bytes: int = 0, request_bytes: int = 0):
+        c = kc_server_config()
+        load().kc_server_config_default(ctypes.byref(c))
+        c.workers, c.budget_bytes, c.request_bytes = workers, budget_bytes, request_bytes
+        self.h = _P()
+        _check(load().kc_server_create(ctypes.byref(c), ctypes.byref(self.h)), "kc_server_create")
+
+    def add_graph(self, g, cfg: kc_config | None = None, pool_seed: int = 0,
+                  pool_trees: int = 0) -> int:
+        row_off = np.ascontiguousarray(g.row_off, dtype=np.int64)
+        col = np.ascontiguousarray(g.col, dtype=np.int32)
+        gid = ctypes.c_int32(-1)
+        _check(load().kc_server_add_graph(self.h, row_off.shape[0] - 1, _ptr(row_off), _ptr(col),
+                                          None if cfg is None else ctypes.byref(cfg), pool_seed,
+                                          pool_trees, ctypes.byref(gid)), "kc_server_add_graph")
+        return gid.value
+
+    def query(self, graph: int, seed: int, eps: float, delta: float) -> int:
+        t = ctypes.c_int64(-1)
+        _check(load().kc_server_submit_query(self.h, graph, seed, eps, delta, ctypes.byref(t)),
+               "kc_server_submit_query")
+        return t.value
+
+    def pool_query(self, graph: int, eps: float, delta: float) -> int:
+        t = ctypes.c_int64(-1)
+        _check(load().kc_server_submit_pool_query(self.h, graph, eps, delta, ctypes.byref(t)),
+               "kc_server_submit_pool_query")
+        return t.value
+
+    def update(self, graph: int, ops, mode: int = KC_UPDATE_ISM) -> int:
+        arr, k = _edge_ops(ops)
+        t = ctypes.c_int64(-1)
+        _check(load().kc_server_submit_update(self.h, graph, arr, k, mode, ctypes.byref(t)),
+               "kc_server_submit_update")
+        return t.value
+
+    def wait(self, ticket: int) -> dict:
+        info = kc_request_info()
+        _check(load().kc_server_wait(self.h, ticket, ctypes.byref(info)), "kc_server_wait")
+        return info.as_dict()
+
+    def poll(self, ticket: int):
+        info = kc_request_info()
+        done = ctypes.c_int32(0)
+        _check(load().kc_server_poll(self.h, ticket, ctypes.byref(done), ctypes.byref(info)),
+               "kc_server_poll")
+        return info.as_dict() if done.value else None
+
+    def drain(self):
+        _check(load().kc_server_drain(self.h), "kc_server_drain")
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().kc_server_destroy(self.h)
             self.h = None
 
     def __del__(self):

@@ -1,4 +1,4 @@
-"""The C-ABI library loads and exports every entry point include/kc.h declares
+"""The C-ABI library loads and exports every entry point include/*.h declares
 (no compute calls: these run without a GPU)."""
 import os
 import re
@@ -6,13 +6,16 @@ import re
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-HEADER = os.path.join(ROOT, "include", "kc.h")
+HEADERS = [os.path.join(ROOT, "include", h) for h in ("kc.h", "kc_serve.h")]
 
 
 def _declared():
-    src = open(HEADER).read()
-    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(kc_[a-z0-9_]+)\s*\(", src)))
+    names = set()
+    for h in HEADERS:
+        src = open(h).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        names.update(re.findall(r"\b(kc_[a-z0-9_]+)\s*\(", src))
+    return sorted(names)
 
 
 @pytest.fixture(scope="module")
@@ -82,3 +85,14 @@ def test_no_device_is_reported(lib):
     st, h = kc.kc_graph_create(g.row_off, g.col, check=False)
     assert kc.STATUS[st] == "KC_ERR_NO_DEVICE" and not h
     assert np.all(g.deg == 2)
+
+
+def test_server_config_defaults(lib):
+    import ctypes
+
+    from paper_2511_16356_gb300 import kc
+
+    c = kc.kc_server_config()
+    lib.kc_server_config_default(ctypes.byref(c))
+    assert c.struct_size == ctypes.sizeof(kc.kc_server_config)
+    assert c.workers == 4 and c.budget_bytes == 0 and c.request_bytes == 0
