@@ -184,6 +184,104 @@ def run_reference(args):
 
 WALKER_NAMES = {1: "lane", 2: "warp", 3: "hybrid"}
 
+
+def serve_workload(n_graphs: int, n_max: int, seed: int = 3):
+    """Mixed resident graphs: ER, perturbed grids and Chung-Lu graphs with n
+    log-uniform on [1e3, n_max] (seeded)."""
+    from paper_2511_16356_gb300 import synth as S
+
+    rng = np.random.default_rng(seed)
+    gs = []
+    for i in range(n_graphs):
+        n = int(np.exp(rng.uniform(np.log(1e3), np.log(n_max))))
+        kind = i % 3
+        if kind == 0:
+            gs.append(S.er_lcc(n, 8.0 / n, 100 + i))
+        elif kind == 1:
+            w = max(8, int(np.sqrt(n)))
+            gs.append(S.grid_perturbed(w, max(8, n // w), 0.25, 100 + i))
+        else:
+            gs.append(S.chung_lu(n, 2.1, 10.0, 100 + i))
+    return gs
+
+
+def serve_leg(args, kc):
+    """Served (continuous batching, `--serve-workers` streams) against the plain
+    one-graph-per-call path on the same Poisson stream of Kemeny queries."""
+    gs = serve_workload(args.serve_graphs, args.serve_nmax)
+    rng = np.random.default_rng(7)
+    Q = args.serve_queries
+    q_graph = rng.integers(0, len(gs), size=Q)
+    q_eps = rng.choice([0.05, 0.02, 0.01], size=Q)
+    q_seed = 1000 + np.arange(Q)
+    delta = 0.05
+    cfg = kc.kc_config_default()
+    cfg.keep_trees = 0
+    handles = [kc.KemenyGraph.from_graph(g, cfg) for g in gs]
+
+    def plain_one(i):
+        G = handles[int(q_graph[i])]
+        G.reset(int(q_seed[i]))
+        return G.estimate(float(q_eps[i]), delta)
+
+    for i in range(min(8, Q)):  # warm-up
+        plain_one(i)
+    t = time.perf_counter()
+    for i in range(Q):
+        plain_one(i)
+    closed = time.perf_counter() - t
+    rate = args.serve_load * Q / closed  # offered load: a multiple of the plain capacity
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, size=Q))
+
+    # plain: one query at a time in arrival order (latency includes queueing)
+    lat_p, k_p = [], []
+    t0 = time.perf_counter()
+    for i in range(Q):
+        now = time.perf_counter() - t0
+        if now < arrivals[i]:
+            time.sleep(arrivals[i] - now)
+        k_p.append(plain_one(i))
+        lat_p.append(time.perf_counter() - t0 - arrivals[i])
+    span_p = time.perf_counter() - t0
+    for G in handles:
+        G.close()
+
+    # served: submit at arrival, workers overlap requests on the device
+    lat_s, k_s = [], []
+    with kc.Server(workers=args.serve_workers) as srv:
+        ids = [srv.add_graph(g, cfg) for g in gs]
+        for i in range(min(8, Q)):  # warm-up
+            srv.wait(srv.query(ids[int(q_graph[i])], int(q_seed[i]), float(q_eps[i]), delta))
+        tickets = []
+        t0 = time.perf_counter()
+        for i in range(Q):
+            now = time.perf_counter() - t0
+            if now < arrivals[i]:
+                time.sleep(arrivals[i] - now)
+            tickets.append((time.perf_counter() - t0,
+                            srv.query(ids[int(q_graph[i])], int(q_seed[i]), float(q_eps[i]),
+                                      delta)))
+        for i, (t_sub, tk) in enumerate(tickets):
+            info = srv.wait(tk)
+            k_s.append(info["K"])
+            lat_s.append((info["t_end_ms"] - info["t_submit_ms"]) / 1000.0 + t_sub - arrivals[i])
+        span_s = time.perf_counter() - t0
+
+    def summ(lat, span):
+        a = np.asarray(lat) * 1000.0
+        return {"p50_ms": float(np.percentile(a, 50)), "p99_ms": float(np.percentile(a, 99)),
+                "qps": Q / span}
+
+    return {
+        "workload": f"{len(gs)} resident graphs (ER / perturbed grid / Chung-Lu, n log-uniform "
+                    f"on [1e3, {args.serve_nmax:.0e}]), {Q} Kemeny queries, Poisson arrivals at "
+                    f"{args.serve_load}x the plain path's capacity, eps in {{5%, 2%, 1%}}, "
+                    f"delta {delta}",
+        "offered_qps": rate, "workers": args.serve_workers,
+        "served": summ(lat_s, span_s), "plain": summ(lat_p, span_p),
+        "identical_results": bool(np.array_equal(np.asarray(k_s), np.asarray(k_p))),
+    }
+
 # DRAM bytes per Wilson departure of k_wilson_warp on road-shaped grids: an ncu
 # capture (dram__bytes) of the kernel on the 300x300 perturbed grid with 1000
 # trees in flight moved 9.70 GB for 1.133e9 departures.  The full-size launch
@@ -216,6 +314,13 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-tte", action="store_true")
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--serve-graphs", type=int, default=48)
+    ap.add_argument("--serve-nmax", type=float, default=3e4)
+    ap.add_argument("--serve-queries", type=int, default=96)
+    ap.add_argument("--serve-workers", type=int, default=8)
+    ap.add_argument("--serve-load", type=float, default=1.5,
+                    help="offered query rate as a multiple of the plain path's capacity")
     args = ap.parse_args()
     if args.warmup < 3:
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
@@ -381,6 +486,10 @@ def main():
                       "steps": k_e2e,
                       "includes": "kc_graph_create from pinned host CSR (validation, "
                                   "records, BFS tau0, DFN), kc_sample, f read back, destroy"}
+
+    # ---- served p50/p99 against the plain path (rank 0)
+    if not args.no_serve and rank == 0:
+        out["serve"] = serve_leg(args, kc)
 
     # ---- the CPU oracle on the host cores (rank 0, N = 1 only)
     if not args.no_cpu_baseline and rank == 0 and ws == 1:

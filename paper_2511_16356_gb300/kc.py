@@ -285,6 +285,18 @@ def kc_stats(g) -> dict:
     return s.as_dict()
 
 
+def kc_graph_reset(g, seed: int, sample_id_base: int = 0) -> None:
+    _check(load().kc_graph_reset(g, seed, sample_id_base), "kc_graph_reset", g)
+
+
+def kc_graph_set_workspace_limit(g, nbytes: int) -> None:
+    _check(load().kc_graph_set_workspace_limit(g, nbytes), "kc_graph_set_workspace_limit", g)
+
+
+def kc_graph_release_workspace(g) -> None:
+    _check(load().kc_graph_release_workspace(g), "kc_graph_release_workspace", g)
+
+
 def kc_reset_timers(g) -> None:
     _check(load().kc_reset_timers(g), "kc_reset_timers", g)
 
@@ -321,6 +333,9 @@ class KemenyGraph:
 
     def tau0(self) -> dict:
         return kc_get_tau0(self.h, self.n)
+
+    def reset(self, seed: int, sample_id_base: int = 0):
+        kc_graph_reset(self.h, seed, sample_id_base)
 
     def stats(self) -> dict:
         return kc_stats(self.h)
