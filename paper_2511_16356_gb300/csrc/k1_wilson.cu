@@ -240,7 +240,8 @@ __global__ void __launch_bounds__(kWarpWalkerBlock, 24) k_wilson_warp(GraphView 
                                                      const int32_t *__restrict__ sorder,
                                                      int64_t step_cap, int64_t iter_cap,
                                                      const int32_t *__restrict__ rs_q,
-                                                     const int32_t *__restrict__ rs_pos) {
+                                                     const int32_t *__restrict__ rs_pos,
+                                                     volatile int32_t *done_flag) {
     const unsigned kFull = 0xFFFFFFFFu;
     const int lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
@@ -471,18 +472,28 @@ __global__ void __launch_bounds__(kWarpWalkerBlock, 24) k_wilson_warp(GraphView 
         w.steps[t] = (rs_q ? w.steps[t] : 0) + tot;
         atomicMax(w.maxdepth, md);
     }
+    if (done_flag) {
+        // publish the finished tree (its depth + 1) to the host, after every
+        // lane's words and order entries are visible
+        __threadfence_system();
+        __syncwarp();
+        if (lane == 0) {
+            __threadfence_system();
+            done_flag[t] = md + 1;
+        }
+    }
 }
 
 }  // namespace
 
 cudaError_t launch_wilson_warp(const GraphView &g, WaveView w, uint64_t seed, const int64_t *sids,
                                const int32_t *sorder, int64_t step_cap, cudaStream_t s,
-                               const int32_t *rs_q, const int32_t *rs_pos) {
+                               const int32_t *rs_q, const int32_t *rs_pos, int32_t *done_flag) {
     // a correct run needs at most about 3 iterations per departure (walk,
     // count, commit / pop), however the walkers serialise
     const int64_t iter_cap = 4 * step_cap + 64 * g.n + 4096;
     k_wilson_warp<<<(unsigned)w.B, kWarpWalkerBlock, 0, s>>>(
-        g, w, seed, sids, sorder, step_cap, iter_cap, rs_q, rs_pos);
+        g, w, seed, sids, sorder, step_cap, iter_cap, rs_q, rs_pos, done_flag);
     return cudaGetLastError();
 }
 

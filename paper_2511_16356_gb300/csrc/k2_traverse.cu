@@ -38,8 +38,8 @@ __global__ void __launch_bounds__(128) k_bottom_up(GraphView g, WaveView w) {
     const int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (t >= w.B) return;
     const int64_t n = g.n;
-    const int32_t *__restrict__ ord = w.ord + t * n;
-    const uint64_t *__restrict__ word = w.word + t * n;
+    const int32_t *__restrict__ ord = w.ord + wave_tree(w, t) * n;
+    const uint64_t *__restrict__ word = w.word + wave_tree(w, t) * n;
     int32_t *size = w.size + t * n;
     int64_t *vol = w.vol + t * n;
     for (int64_t base = n - 1; base >= 0; base -= 32) {
@@ -100,7 +100,7 @@ __device__ __forceinline__ int32_t parent_of(const uint64_t *word, int64_t v) {
 __global__ void k_tree_prep(GraphView g, WaveView w) {
     const int64_t n = g.n;
     const int64_t t = blockIdx.y;
-    uint64_t *word = w.word + t * n;
+    uint64_t *word = w.word + wave_tree(w, t) * n;
     int32_t *size = w.size + t * n;
     int64_t *vol = w.vol + t * n;
     int32_t *din = w.din + t * n;
@@ -116,7 +116,7 @@ __global__ void k_tree_prep(GraphView g, WaveView w) {
 __global__ void k_child_count(GraphView g, WaveView w) {
     const int64_t n = g.n;
     const int64_t t = blockIdx.y;
-    uint64_t *word = w.word + t * n;
+    uint64_t *word = w.word + wave_tree(w, t) * n;
     int32_t *din = w.din + t * n;
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
          v += (int64_t)gridDim.x * blockDim.x) {
@@ -131,7 +131,7 @@ __global__ void k_child_count(GraphView g, WaveView w) {
 __global__ void k_leaf_up(GraphView g, WaveView w) {
     const int64_t n = g.n;
     const int64_t t = blockIdx.y;
-    uint64_t *word = w.word + t * n;
+    uint64_t *word = w.word + wave_tree(w, t) * n;
     int32_t *size = w.size + t * n;
     int64_t *vol = w.vol + t * n;
     int32_t *din = w.din + t * n;
@@ -178,8 +178,8 @@ __global__ void __launch_bounds__(128) k_bottom_up_offsets(GraphView g, WaveView
     const int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (t >= w.B) return;
     const int64_t n = g.n;
-    const int32_t *__restrict__ ord = w.ord + t * n;
-    const uint64_t *__restrict__ word = w.word + t * n;
+    const int32_t *__restrict__ ord = w.ord + wave_tree(w, t) * n;
+    const uint64_t *__restrict__ word = w.word + wave_tree(w, t) * n;
     int32_t *size = w.size + t * n;
     int64_t *vol = w.vol + t * n;
     int32_t *din = w.din + t * n;
@@ -238,7 +238,7 @@ __global__ void __launch_bounds__(128) k_sibling_offsets(GraphView g, WaveView w
     const int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (t >= w.B) return;
     const int64_t n = g.n;
-    const uint64_t *__restrict__ word = w.word + t * n;
+    const uint64_t *__restrict__ word = w.word + wave_tree(w, t) * n;
     const int32_t *__restrict__ size = w.size + t * n;
     int32_t *din = w.din + t * n;
     int32_t *run = w.aux + t * n;  // per-parent running sum of sizes, zeroed
@@ -272,8 +272,8 @@ __global__ void __launch_bounds__(128) k_top_down(GraphView g, WaveView w, int w
     const int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (t >= w.B) return;
     const int64_t n = g.n;
-    const int32_t *__restrict__ ord = w.ord + t * n;
-    const uint64_t *__restrict__ word = w.word + t * n;
+    const int32_t *__restrict__ ord = w.ord + wave_tree(w, t) * n;
+    const uint64_t *__restrict__ word = w.word + wave_tree(w, t) * n;
     int32_t *din = w.din + t * n;
     int32_t *pre = w.aux + t * n;
     // software pipeline: the order two chunks ahead and the parent and offset

@@ -30,7 +30,7 @@ __global__ void __launch_bounds__(256) k_ttf_scan(GraphView g, WaveView w) {
     const int64_t t = blockIdx.y;
     const int64_t n = g.n;
     const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const uint64_t *__restrict__ word = w.word + t * n;
+    const uint64_t *__restrict__ word = w.word + wave_tree(w, t) * n;
     const int32_t *__restrict__ din = w.din + t * n;
     const int32_t *__restrict__ size = w.size + t * n;
     const int64_t *__restrict__ vol = w.vol + t * n;
@@ -63,7 +63,7 @@ __global__ void __launch_bounds__(256) k_ttf_scan(GraphView g, WaveView w) {
     if (threadIdx.x == 0) {
         long long s = 0;
         for (int k = 0; k < (int)(blockDim.x >> 5); ++k) s += part[k];
-        if (s != 0) atomicAdd((unsigned long long *)(w.f + t), (unsigned long long)s);
+        if (s != 0) atomicAdd((unsigned long long *)(w.f + wave_tree(w, t)), (unsigned long long)s);
     }
 }
 
@@ -96,7 +96,7 @@ __global__ void __launch_bounds__(128) k_ttf_bit(GraphView g, WaveView w) {
     const int64_t n = g.n;
     const int32_t r = g.root;
     const int32_t twom = (int32_t)g.twom;  // host guarantees 2m < 2^31 for this kernel
-    const uint64_t *__restrict__ word = w.word + t * n;
+    const uint64_t *__restrict__ word = w.word + wave_tree(w, t) * n;
     const int32_t *__restrict__ size = w.size + t * n;
     const int64_t *__restrict__ vol = w.vol + t * n;
     const int32_t *__restrict__ pre = w.aux + t * n;
@@ -209,14 +209,16 @@ __global__ void __launch_bounds__(128) k_ttf_bit(GraphView g, WaveView w) {
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) facc += __shfl_down_sync(kFull, facc, o);
-    if (lane == 0) w.f[t] = facc;
+    if (lane == 0) w.f[wave_tree(w, t)] = facc;
 }
 
 }  // namespace
 
 cudaError_t launch_ttf_scan(const GraphView &g, WaveView w, cudaStream_t s) {
-    cudaError_t e = cudaMemsetAsync(w.f, 0, sizeof(int64_t) * (size_t)w.B, s);
-    if (e != cudaSuccess) return e;
+    if (!w.tmap) {  // with a tree map the caller has zeroed f for the whole wave
+        cudaError_t e = cudaMemsetAsync(w.f, 0, sizeof(int64_t) * (size_t)w.B, s);
+        if (e != cudaSuccess) return e;
+    }
     dim3 grid((unsigned)((g.n + 255) / 256), (unsigned)w.B);
     k_ttf_scan<<<grid, 256, 0, s>>>(g, w);
     return cudaGetLastError();

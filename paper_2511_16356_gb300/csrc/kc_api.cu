@@ -6,6 +6,9 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <thread>
+#include <chrono>
+#include <array>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -255,14 +258,15 @@ Plan plan_for(kc_graph *g, int64_t ntrees, bool canon = true) {
 
 // DFS stack of the BIT variant: one entry per stacked ancestor, so the
 // deepest tree's depth + 2 entries per tree suffice.
-void ensure_stack(kc_graph *g, Plan &p, uint32_t maxdepth) {
+void ensure_stack(kc_graph *g, Plan &p, uint32_t maxdepth, cudaStream_t st = nullptr) {
+    if (!st) st = g->stream;
     const int64_t need_cap = (int64_t)maxdepth + 2;
     const size_t need = sizeof(int32_t) * 4 * (size_t)need_cap * (size_t)p.BT;
     if (need > g->stack_bytes) {
-        if (g->d_stack) KC_CK(g, cudaFreeAsync(g->d_stack, g->stream));
+        if (g->d_stack) KC_CK(g, cudaFreeAsync(g->d_stack, st));
         g->d_stack = nullptr;
         g->stack_bytes = 0;
-        KC_CK(g, cudaMallocAsync((void **)&g->d_stack, need, g->stream));
+        KC_CK(g, cudaMallocAsync((void **)&g->d_stack, need, st));
         g->stack_bytes = need;
     }
     p.stack_cap = need_cap;
@@ -311,7 +315,167 @@ int wilson_launches(const kc_graph *g) { return g->walker == KC_WALK_HYBRID ? 2 
 
 // One full sampling pass over sample ids [sid0, sid0 + B): walk, traverse,
 // evaluate f.  Leaves per-tree results in the carved workspace.
+// Completion flags (host-mapped), tree-map staging and the second stream of
+// pipelined waves, sized for B trees.
+void ensure_pipeline(kc_graph *g, int64_t B) {
+    if (!g->stream2) KC_CK(g, cudaStreamCreateWithFlags(&g->stream2, cudaStreamNonBlocking));
+    if (B <= g->done_cap) return;
+    if (g->h_done) cudaFreeHost(g->h_done);
+    if (g->h_map) cudaFreeHost(g->h_map);
+    dfree(g->d_map);
+    g->h_done = g->h_map = g->d_done = nullptr;
+    g->done_cap = 0;
+    KC_CK(g, cudaHostAlloc((void **)&g->h_done, sizeof(int32_t) * (size_t)B, cudaHostAllocMapped));
+    KC_CK(g, cudaHostGetDevicePointer((void **)&g->d_done, g->h_done, 0));
+    KC_CK(g, cudaMallocHost((void **)&g->h_map, sizeof(int32_t) * (size_t)B));
+    dalloc(g, &g->d_map, (size_t)B);
+    g->done_cap = B;
+}
+
+// A wave whose traversal and TTF start on a second stream while the walk is
+// still running: the 32-walker kernel flags every finished tree in host-mapped
+// memory, the host gathers finished trees into chunks of up to BT (a tree map
+// per chunk) and launches their sub-wave kernels; only the chunk holding the
+// slowest trees waits for the end of the walk.
+void run_wave_pipelined(kc_graph *g, Plan &p, int64_t B, int64_t sid0) {
+    ensure_pipeline(g, B);
+    GraphView gv = view_of(g);
+    Carved c = carve(g, p);
+    WaveView w = c.wv;
+    w.B = B;
+    cudaStream_t s1 = g->stream, s2 = g->stream2;
+    std::vector<cudaEvent_t> evs;
+    auto event = [&]() {
+        cudaEvent_t e = nullptr;
+        KC_CK(g, cudaEventCreate(&e));
+        evs.push_back(e);
+        return e;
+    };
+    struct EvGuard {
+        std::vector<cudaEvent_t> &v;
+        ~EvGuard() {
+            for (cudaEvent_t e : v) cudaEventDestroy(e);
+        }
+    } guard{evs};
+    volatile int32_t *hd = g->h_done;
+    for (int64_t t = 0; t < B; ++t) hd[t] = 0;
+    KC_CK(g, cudaMemsetAsync(g->d_err, 0, 2 * sizeof(uint32_t), s1));
+    KC_CK(g, cudaMemsetAsync(w.f, 0, sizeof(int64_t) * (size_t)B, s1));
+    KC_CK(g, launch_iota(c.sids, sid0, B, s1));
+    {
+        Phase ph(g, g->t_init);
+        KC_CK(g, launch_wave_init(gv, w, s1));
+        ph.done(1);
+    }
+    cudaEvent_t ev_ready = event(), ev_w0 = event(), ev_w1 = event();
+    KC_CK(g, cudaEventRecord(ev_ready, s1));
+    KC_CK(g, cudaStreamWaitEvent(s2, ev_ready, 0));
+    KC_CK(g, cudaEventRecord(ev_w0, s1));
+    KC_CK(g, launch_wilson_warp(gv, w, g->seed, c.sids, g->d_sorder, step_cap_of(g), s1, nullptr,
+                                nullptr, g->d_done));
+    KC_CK(g, cudaEventRecord(ev_w1, s1));
+    const int64_t chunk_min = std::max<int64_t>(1, std::min<int64_t>(p.BT, (B + 1) / 2));
+    std::vector<int32_t> unseen((size_t)B), ready;
+    for (int64_t t = 0; t < B; ++t) unseen[(size_t)t] = (int32_t)t;
+    std::vector<std::array<cudaEvent_t, 3>> chunk_ev;
+    int64_t processed = 0;
+    bool wdone = false;
+    while (processed < B) {
+        if (!wdone) {
+            const cudaError_t q = cudaEventQuery(ev_w1);
+            if (q == cudaSuccess) wdone = true;
+            else if (q != cudaErrorNotReady) KC_CK(g, q);
+        }
+        size_t keep = 0;
+        for (size_t i = 0; i < unseen.size(); ++i) {
+            const int32_t t = unseen[i];
+            if (hd[t] != 0) ready.push_back(t);
+            else unseen[keep++] = t;
+        }
+        unseen.resize(keep);
+        if ((int64_t)ready.size() >= (wdone ? 1 : chunk_min)) {
+            const int64_t b = std::min<int64_t>(p.BT, (int64_t)ready.size());
+            int32_t md = 0;
+            for (int64_t k = 0; k < b; ++k) {
+                const int32_t t = ready[(size_t)k];
+                g->h_map[processed + k] = t;
+                md = std::max(md, hd[t] - 1);
+            }
+            ready.erase(ready.begin(), ready.begin() + b);
+            KC_CK(g, cudaMemcpyAsync(g->d_map + processed, g->h_map + processed,
+                                     sizeof(int32_t) * (size_t)b, cudaMemcpyHostToDevice, s2));
+            if (p.bit) {
+                ensure_stack(g, p, (uint32_t)md, s2);
+                c = carve(g, p);
+            }
+            WaveView sv = c.wv;
+            sv.B = b;
+            sv.tmap = g->d_map + processed;
+            std::array<cudaEvent_t, 3> e3 = {event(), event(), event()};
+            KC_CK(g, cudaEventRecord(e3[0], s2));
+            int nl = 0;
+            KC_CK(g, launch_traverse(gv, sv, p.bit, s2, &nl, fast_traversal(g)));
+            g->t_traverse.launches += nl;
+            KC_CK(g, cudaEventRecord(e3[1], s2));
+            if (p.bit) KC_CK(g, launch_ttf_bit(gv, sv, s2));
+            else KC_CK(g, launch_ttf_scan(gv, sv, s2));
+            g->t_ttf.launches += 1;
+            KC_CK(g, cudaEventRecord(e3[2], s2));
+            chunk_ev.push_back(e3);
+            processed += b;
+            continue;
+        }
+        if (wdone && unseen.empty() && ready.empty()) break;
+        if (wdone && !unseen.empty()) {
+            // the walk is over: every flag is visible now
+            bool any = false;
+            for (int32_t t : unseen) any = any || hd[t] != 0;
+            if (!any) {
+                g->last_error = "a walker finished without flagging its tree";
+                throw Fail{KC_ERR_CUDA};
+            }
+            continue;
+        }
+        std::this_thread::sleep_for(std::chrono::microseconds(100));
+    }
+    cudaEvent_t ev_join = event();
+    KC_CK(g, cudaEventRecord(ev_join, s2));
+    KC_CK(g, cudaStreamWaitEvent(s1, ev_join, 0));
+    KC_CK(g, cudaStreamSynchronize(s1));
+    float ms = 0.f;
+    KC_CK(g, cudaEventElapsedTime(&ms, ev_w0, ev_w1));
+    g->t_wilson.ms += ms;
+    g->t_wilson.launches += 1;
+    for (auto &e3 : chunk_ev) {
+        KC_CK(g, cudaEventElapsedTime(&ms, e3[0], e3[1]));
+        g->t_traverse.ms += ms;
+        KC_CK(g, cudaEventElapsedTime(&ms, e3[1], e3[2]));
+        g->t_ttf.ms += ms;
+    }
+    uint32_t hdr[2] = {0, 0};
+    KC_CK(g, copy_sync(g, hdr, g->d_err, sizeof(hdr), cudaMemcpyDeviceToHost));
+    if (hdr[0] & kErrStepLimit) {
+        g->last_error = "Wilson walk exceeded the step cap";
+        throw Fail{KC_ERR_STEP_LIMIT};
+    }
+    if (hdr[0] & (kErrBadTree | kErrIterLimit)) {
+        g->last_error = "inconsistent tree state, walker iteration cap or traversal stack overflow";
+        throw Fail{KC_ERR_CUDA};
+    }
+}
+
 void run_wave(kc_graph *g, Plan &p, int64_t B, int64_t sid0, bool canonical = false) {
+    if (!canonical && g->walker == KC_WALK_WARP && B > 1) {
+        try {
+            run_wave_pipelined(g, p, B, sid0);
+        } catch (Fail &) {
+            // let both streams drain before the workspace is reused
+            cudaStreamSynchronize(g->stream);
+            if (g->stream2) cudaStreamSynchronize(g->stream2);
+            throw;
+        }
+        return;
+    }
     GraphView gv = view_of(g);
     Carved c = carve(g, p);
     WaveView w = c.wv;
@@ -978,6 +1142,10 @@ kc_status kc_graph_destroy(kc_graph *g) {
     dfree(g->d_sorder);
     dfree(g->d_err);
     if (g->d_scratch) cudaFree(g->d_scratch);
+    if (g->h_done) cudaFreeHost(g->h_done);
+    if (g->h_map) cudaFreeHost(g->h_map);
+    dfree(g->d_map);
+    if (g->stream2) cudaStreamDestroy(g->stream2);
     if (g->ev0) cudaEventDestroy(g->ev0);
     if (g->ev1) cudaEventDestroy(g->ev1);
     delete g;

@@ -168,7 +168,14 @@ struct WaveView {
     int32_t *stack;          // [B][stack_cap] x 4 int32 DFS stack (BIT variant)
     int64_t stack_cap;       // entries per tree
     int32_t pos0 = 1;        // vertices already placed in ord before the walk
+    const int32_t *tmap = nullptr;  // sub-wave tree t -> wave tree tmap[t] (word, ord, f,
+                                    // steps); null: the identity
 };
+
+// wave tree of sub-wave tree t
+__host__ __device__ __forceinline__ int64_t wave_tree(const WaveView &w, int64_t t) {
+    return w.tmap ? (int64_t)w.tmap[t] : t;
+}
 
 // ---------------------------------------------------------------------------
 // Host handle
@@ -230,6 +237,13 @@ struct kc_graph {
     int64_t last_cg_iters = 0;
     kc::PhaseTimer t_wilson, t_traverse, t_ttf, t_reduce, t_update, t_setup, t_init;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    // pipelined waves: a second stream for traversal/TTF chunks, host-mapped
+    // per-tree completion flags written by the walker, the chunks' tree maps
+    cudaStream_t stream2 = nullptr;
+    int32_t *h_done = nullptr, *d_done = nullptr;  // mapped pinned host memory
+    int32_t *h_map = nullptr;                      // pinned staging of tree maps
+    int32_t *d_map = nullptr;
+    int64_t done_cap = 0;
     std::string last_error;
 };
 
@@ -261,7 +275,8 @@ cudaError_t launch_wilson(const GraphView &g, WaveView w, uint64_t seed, const i
                           unsigned int *done = nullptr, int64_t q_stop = 0, int64_t stop_at = 0);
 cudaError_t launch_wilson_warp(const GraphView &g, WaveView w, uint64_t seed, const int64_t *sids,
                                const int32_t *sorder, int64_t step_cap, cudaStream_t s,
-                               const int32_t *rs_q = nullptr, const int32_t *rs_pos = nullptr);
+                               const int32_t *rs_q = nullptr, const int32_t *rs_pos = nullptr,
+                               int32_t *done_flag = nullptr);
 // Traversal modes: kTravCanonical numbers children in ascending id (the DFN the
 // oracle reports and the update kernels enumerate by); the others give some
 // valid DFN (enough for f): kTravChunked (warp per tree, for deep trees and
