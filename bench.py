@@ -284,9 +284,9 @@ def serve_leg(args, kc):
 
 # DRAM bytes per Wilson departure of k_wilson_warp on road-shaped grids: an ncu
 # capture (dram__bytes) of the kernel on the 300x300 perturbed grid with 1000
-# trees in flight moved 9.70 GB for 1.133e9 departures.  The full-size launch
+# trees in flight moved 10.27 GB for 1.133e9 departures.  The full-size launch
 # is too long to capture; its traffic is this figure times its departures.
-WILSON_WARP_GRID_DRAM_BYTES_PER_STEP = 9.70e9 / 1.1334e9
+WILSON_WARP_GRID_DRAM_BYTES_PER_STEP = 10.27e9 / 1.1334e9
 
 
 def main():
