@@ -254,3 +254,21 @@ def test_large_shallow_graphs_bit_exact(name):
         tr = G.tree(5)
         ref = O.tree(g, t0, 21, 5)
         assert np.array_equal(tr["din"], ref.din) and np.array_equal(tr["vol"], ref.vol)
+
+
+@pytest.mark.parametrize("name", ["er300", "grid17x13", "cl3000"])
+def test_pipelined_chunks_bit_exact(name):
+    """A workspace limit small enough for a handful of trees per traversal
+    sub-wave makes the walk's finished trees go through several tree-mapped
+    chunks on the second stream: trees and f unchanged."""
+    g = SMALL[name]()
+    t0 = O.tau0(g)
+    with kc.KemenyGraph.from_graph(g, _cfg(keep_trees=0)) as G:
+        kc.kc_graph_set_workspace_limit(G.h, 40 * 40 * g.n + 4096)
+        G.sample(31, 120)
+        st = G.stats()
+        assert st["walker"] == kc.KC_WALK_WARP and st["trees_in_flight"] < 120
+        got = G.samples()
+        f_ref, st_ref = O.sample_batch(g, t0, 31, 0, 120)
+        assert np.array_equal(got["steps"], st_ref)
+        assert np.array_equal(got["f"], f_ref)
