@@ -12,7 +12,7 @@ import threading
 import numpy as np
 
 __all__ = [
-    "build_oracle", "lib", "philox4x32_10", "bounded", "root", "root_smallest_id", "bfs_tree",
+    "build_oracle", "lib", "philox4x32_10", "bounded", "root", "root_smallest_id", "bfs_tree", "dfs_tree",
     "Tau0",
     "tau0", "wilson", "traverse", "f_naive", "f_alg1", "TreeOut", "tree",
     "sample_batch", "num_threads", "STEP_CAP_DEFAULT", "cond_wilson", "select", "link_cut",
@@ -60,6 +60,8 @@ def lib():
             L.orc_root_central.restype = c_i32
             L.orc_bfs_tree.argtypes = [c_i64, vp, vp, c_i32, vp, vp]
             L.orc_bfs_tree.restype = c_i32
+            L.orc_dfs_tree.argtypes = [c_i64, vp, vp, c_i32, vp, vp]
+            L.orc_dfs_tree.restype = c_i32
             L.orc_wilson.argtypes = [c_i64, vp, vp, c_i32, c_u64, c_u32, vp, vp, vp, c_i64]
             L.orc_wilson.restype = ctypes.c_int
             L.orc_traverse.argtypes = [c_i64, vp, vp, c_i32, vp, vp, vp, vp, vp]
@@ -123,6 +125,14 @@ def bfs_tree(g, r: int):
     return p0, level, int(ecc)
 
 
+def dfs_tree(g, r: int):
+    """Depth-first spanning tree from r, rows scanned in ascending id (Exp-II)."""
+    p0 = np.empty(g.n, dtype=np.int32)
+    level = np.empty(g.n, dtype=np.int32)
+    deepest = lib().orc_dfs_tree(g.n, _p(g.row_off), _p(g.col), r, _p(p0), _p(level))
+    return p0, level, int(deepest)
+
+
 class TreeOut:
     """Per-tree outputs: parent, depth, size, vol, DFN in/out, steps, f."""
 
@@ -138,11 +148,26 @@ class TreeOut:
 
 
 class Tau0:
-    """Root r, BFS tree tau0 (parent p0, DFN in0/out0, volumes), ecc(r)."""
+    """Root r, path tree tau0 (parent p0, DFN in0/out0, volumes) and its depth
+    `ecc`.  kind: "bfs" (Algorithm 1; depth = ecc(r)), "dfs" or "wilson" (the
+    other path selections of Exp-II; "wilson" is the uniform tree of sample id 0
+    under `seed`).  Theorem 4 holds for any fixed spanning tree tau0."""
 
-    def __init__(self, g, r=None):
+    def __init__(self, g, r=None, kind: str = "bfs", seed: int = 0):
         self.r = root(g) if r is None else int(r)
-        self.p0, self.level, self.ecc = bfs_tree(g, self.r)
+        self.kind = kind
+        if kind == "bfs":
+            self.p0, self.level, self.ecc = bfs_tree(g, self.r)
+        elif kind == "dfs":
+            self.p0, self.level, self.ecc = dfs_tree(g, self.r)
+        elif kind == "wilson":
+            parent, _ = wilson(g, self.r, seed, 0)
+            self.p0 = parent.astype(np.int32)
+            t = traverse(g, self.r, self.p0)
+            self.level = t.depth.copy()
+            self.ecc = int(self.level.max())
+        else:
+            raise ValueError(kind)
         if self.ecc < 0:
             raise ValueError("graph is disconnected")
         t = TreeOut(g.n)
@@ -152,8 +177,8 @@ class Tau0:
         self.in0, self.out0, self.vol0, self.size0 = t.din, t.dout, t.vol, t.size
 
 
-def tau0(g, r=None) -> Tau0:
-    return Tau0(g, r)
+def tau0(g, r=None, kind: str = "bfs", seed: int = 0) -> Tau0:
+    return Tau0(g, r, kind, seed)
 
 
 def wilson(g, r: int, seed: int, sample: int, order=None, cap: int = STEP_CAP_DEFAULT):

@@ -214,6 +214,45 @@ int32_t orc_bfs_tree(int64_t n, const int64_t *row_off, const int32_t *col, int3
     return ecc;
 }
 
+/*
+ * Depth-first spanning tree from r (the DFS path selection of Exp-II): the
+ * recursive DFS that scans each adjacency row in ascending id and descends
+ * into the first unvisited neighbour, run with an explicit stack of (vertex,
+ * next row position).  p0 = DFS parent (-1 at r), level = depth in the DFS
+ * tree.  Returns the largest depth, or -1 if some vertex is unreachable.
+ */
+int32_t orc_dfs_tree(int64_t n, const int64_t *row_off, const int32_t *col, int32_t r,
+                     int32_t *p0, int32_t *level) {
+    int32_t *sv = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+    int64_t *se = (int64_t *)malloc(sizeof(int64_t) * (size_t)n);
+    for (int64_t v = 0; v < n; ++v) { level[v] = -1; p0[v] = -1; }
+    int64_t sp = 0, seen = 1;
+    int32_t deepest = 0;
+    level[r] = 0;
+    sv[0] = r;
+    se[0] = row_off[r];
+    while (sp >= 0) {
+        const int32_t u = sv[sp];
+        if (se[sp] < row_off[u + 1]) {
+            const int32_t w = col[se[sp]++];
+            if (level[w] < 0) {
+                p0[w] = u;
+                level[w] = level[u] + 1;
+                if (level[w] > deepest) deepest = level[w];
+                ++seen;
+                ++sp;
+                sv[sp] = w;
+                se[sp] = row_off[w];
+            }
+        } else {
+            --sp;
+        }
+    }
+    free(sv);
+    free(se);
+    return seen == n ? deepest : -1;
+}
+
 /* ------------------------------------------------------------------------ */
 /* Wilson's algorithm                                                        */
 /* ------------------------------------------------------------------------ */

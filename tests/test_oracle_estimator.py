@@ -205,3 +205,55 @@ def test_printed_undo_is_wrong_corrected_is_right():
             wrong += _alg1_as_printed(g, t0, t.parent, t.vol) != naive
             total += 1
     assert wrong > total // 2, "the printed reverse-case undo should disagree on most trees"
+
+
+def _dfs_recursive(g, r):
+    """Textbook recursive DFS (rows in ascending id), written independently of
+    the oracle's explicit-stack version."""
+    import sys
+
+    sys.setrecursionlimit(max(10000, 4 * g.n))
+    parent = [-2] * g.n
+    depth = [0] * g.n
+
+    def visit(u):
+        for e in range(int(g.row_off[u]), int(g.row_off[u + 1])):
+            w = int(g.col[e])
+            if parent[w] == -2:
+                parent[w] = u
+                depth[w] = depth[u] + 1
+                visit(w)
+
+    parent[r] = -1
+    visit(r)
+    return np.array(parent, dtype=np.int32), np.array(depth, dtype=np.int32)
+
+
+@pytest.mark.parametrize("gname", ["grid6x5", "er60", "K7", "star9"])
+def test_dfs_path_tree_matches_recursive_dfs(gname):
+    g = {"grid6x5": lambda: S.grid(6, 5), "er60": lambda: S.er_lcc(60, 0.1, 3),
+         "K7": lambda: S.complete(7), "star9": lambda: S.star(9)}[gname]()
+    t0 = O.tau0(g, kind="dfs")
+    p, d = _dfs_recursive(g, t0.r)
+    assert np.array_equal(t0.p0, p) and np.array_equal(t0.level, d)
+    assert t0.ecc == d.max()
+
+
+@pytest.mark.parametrize("kind", ["dfs", "wilson"])
+@pytest.mark.parametrize("name", ["K4", "grid3x3", "rc7"])
+def test_unbiased_for_dfs_and_wilson_path_trees(name, kind):
+    """Exp-II's other path selections: for a DFS tree or a Wilson tree as tau0,
+    the uniform average of f/(2m) over every spanning tree is still exactly K
+    (Theorem 4 holds for any fixed tau0), and Algorithm 1 equals the naive
+    form tree by tree."""
+    g = {"K4": lambda: S.complete(4), "grid3x3": lambda: S.grid(3, 3),
+         "rc7": lambda: S.random_connected(7, 0.5, 2)}[name]()
+    t0 = O.tau0(g, kind=kind, seed=9)
+    fs = []
+    for T in O.spanning_trees(g):
+        par = O.orient(g.n, T, t0.r)
+        t = O.traverse(g, t0.r, par)
+        a = O.f_alg1(g, t0, par, t.vol)
+        assert a == O.f_naive(g, t0, par, t.vol)
+        fs.append(a)
+    assert np.mean(fs) / (2 * g.m) == pytest.approx(O.K_dense(g), rel=1e-12)
