@@ -91,6 +91,12 @@ enum { KC_WALK_AUTO = 0,       /* WARP                                          
                                   rest; LANE trees still running when a share of the
                                   wave has finished are also handed to WARP          */
 
+/* Path tree tau0 (Algorithm 1 uses BFS; Exp-II compares DFS and Wilson trees).
+   Theorem 4 holds for any fixed spanning tree; shorter paths give lower variance. */
+enum { KC_TAU0_BFS = 0,        /* BFS tree, parent = smallest-id neighbour one level up  */
+       KC_TAU0_DFS = 1,        /* depth-first tree, rows scanned in ascending id          */
+       KC_TAU0_WILSON = 2 };   /* uniform tree of sample id 0 under tau0_seed             */
+
 /* Effective resistance source for insertions (Algorithm 2/3 "Compute R(u,v)"). */
 enum { KC_R_CG = 0,            /* FP64 conjugate gradients on the Laplacian, on the device */
        KC_R_GIVEN = 1 };       /* kc_edge_op.r supplies R(u,v) in G + (u,v)               */
@@ -129,6 +135,9 @@ typedef struct {
                                    this many thousandths of the wave's trees have
                                    finished continue as WARP trees (0: default 900;
                                    >= 1000: never)                                  */
+    int32_t tau0_kind;          /* KC_TAU0_*: the path tree (kc_update needs BFS)    */
+    int32_t reserved1;
+    uint64_t tau0_seed;         /* seed of the KC_TAU0_WILSON path tree              */
 } kc_config;
 
 /* Fill *cfg with the defaults listed above. */

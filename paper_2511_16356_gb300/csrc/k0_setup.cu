@@ -161,9 +161,93 @@ __global__ void k_central_pick(int64_t n, const int32_t *deg, int32_t dmax, cons
     atomicMin(best, ((unsigned long long)(uint32_t)e << 32) | (unsigned long long)v);
 }
 
+// Depth-first tree from r (rows in ascending id): one thread with an explicit
+// stack of (vertex, next row position) -- the recursive DFS is inherently
+// sequential.  Every iteration either advances a row position or pops, so the
+// loop ends after at most 2m + n iterations.  level[] must be -1 everywhere.
+__global__ void k_dfs_tree(GraphView g, int32_t r, int32_t *p0, int32_t *level, int32_t *sv,
+                           int64_t *se, int32_t *deepest) {
+    if (blockIdx.x != 0 || threadIdx.x != 0) return;
+    const int64_t *__restrict__ row_off = g.row_off;
+    const int32_t *__restrict__ col = g.col;
+    int64_t sp = 0;
+    int32_t dmax = 0;
+    level[r] = 0;
+    p0[r] = -1;
+    sv[0] = r;
+    se[0] = row_off[r];
+    const int64_t cap = 2 * g.twom + 2 * g.n + 2;
+    for (int64_t it = 0; sp >= 0 && it < cap; ++it) {
+        const int32_t u = sv[sp];
+        const int64_t e = se[sp];
+        if (e < row_off[u + 1]) {
+            const int32_t w = col[e];
+            se[sp] = e + 1;
+            if (level[w] < 0) {
+                const int32_t lw = level[u] + 1;
+                p0[w] = u;
+                level[w] = lw;
+                dmax = lw > dmax ? lw : dmax;
+                ++sp;
+                sv[sp] = w;
+                se[sp] = row_off[w];
+            }
+        } else {
+            --sp;
+        }
+    }
+    *deepest = dmax;
+}
+
+__global__ void k_fill2(int64_t n, int32_t *a, int32_t *b, int32_t value) {
+    const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v < n) {
+        a[v] = value;
+        b[v] = value;
+    }
+}
+
+// tau0 from a sampled tree's walker words: parent and depth; counts vertices
+// outside the tree and records the largest depth
+__global__ void k_tau0_from_words(int64_t n, const uint64_t *word, int32_t *p0, int32_t *level,
+                                  int32_t *deepest, int32_t *outside) {
+    const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= n) return;
+    const uint64_t x = word[v];
+    if (!w_in_tree(x)) {
+        atomicAdd(outside, 1);
+        p0[v] = -1;
+        level[v] = -1;
+        return;
+    }
+    p0[v] = w_next(x);
+    level[v] = (int32_t)w_count(x);
+    atomicMax(deepest, (int32_t)w_count(x));
+}
+
+__global__ void k_count_negative(int64_t n, const int32_t *a, int32_t *count) {
+    const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v < n && a[v] < 0) atomicAdd(count, 1);
+}
+
 inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
 }  // namespace
+
+cudaError_t launch_dfs_tree(const GraphView &g, int32_t r, int32_t *p0, int32_t *level,
+                            int32_t *sv, int64_t *se, int32_t *deepest, int32_t *unreached,
+                            cudaStream_t s) {
+    k_fill2<<<blocks_for(g.n, 256), 256, 0, s>>>(g.n, p0, level, -1);
+    k_dfs_tree<<<1, 1, 0, s>>>(g, r, p0, level, sv, se, deepest);
+    k_count_negative<<<blocks_for(g.n, 256), 256, 0, s>>>(g.n, level, unreached);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tau0_from_words(int64_t n, const uint64_t *word, int32_t *p0, int32_t *level,
+                                   int32_t *deepest, int32_t *outside, cudaStream_t s) {
+    k_tau0_from_words<<<blocks_for(n, 256), 256, 0, s>>>(n, word, p0, level, deepest, outside);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_argmax_score(int64_t n, const int32_t *la, const int32_t *lb, int mode,
                                 unsigned long long *best, cudaStream_t s) {

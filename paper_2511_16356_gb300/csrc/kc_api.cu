@@ -617,7 +617,7 @@ int32_t central_root(kc_graph *g, int32_t r0, int &launches) {
 // tau0 = BFS tree from g->root over the current device graph (parent = the
 // smallest-id neighbour one level closer), level-synchronous, one launch per
 // level; sets g->ecc.  Throws KC_ERR_DISCONNECTED if a vertex is unreached.
-void build_tau0(kc_graph *g, int &launches) {
+void build_tau0_bfs(kc_graph *g, int &launches) {
     GraphView gv = view_of(g);
     const int64_t n = g->n;
     KC_CK(g, launch_bfs_init(n, g->root, g->d_level0, g->stream));
@@ -646,6 +646,67 @@ void build_tau0(kc_graph *g, int &launches) {
                              g->stream));
     KC_CK(g, cudaStreamSynchronize(g->stream));
     if (unreached) throw Fail{KC_ERR_DISCONNECTED};
+}
+
+// Exp-II's depth-first path tree: one device thread, explicit stack.
+void build_tau0_dfs(kc_graph *g, int &launches) {
+    GraphView gv = view_of(g);
+    const int64_t n = g->n;
+    int32_t *sv = nullptr;
+    int64_t *se = nullptr;
+    KC_CK(g, cudaMallocAsync((void **)&sv, sizeof(int32_t) * (size_t)n, g->stream));
+    KC_CK(g, cudaMallocAsync((void **)&se, sizeof(int64_t) * (size_t)n, g->stream));
+    int32_t *d_cnt = (int32_t *)g->d_scratch;  // [0] deepest, [1] unreached
+    KC_CK(g, cudaMemsetAsync(d_cnt, 0, 2 * sizeof(int32_t), g->stream));
+    KC_CK(g, launch_dfs_tree(gv, g->root, g->d_p0, g->d_level0, sv, se, d_cnt, d_cnt + 1,
+                             g->stream));
+    launches += 3;
+    KC_CK(g, cudaFreeAsync(sv, g->stream));
+    KC_CK(g, cudaFreeAsync(se, g->stream));
+    int32_t h[2] = {0, 0};
+    KC_CK(g, copy_sync(g, h, d_cnt, sizeof(h), cudaMemcpyDeviceToHost));
+    if (h[1]) throw Fail{KC_ERR_DISCONNECTED};
+    g->ecc = h[0];
+}
+
+// Exp-II's Wilson path tree: the uniform tree of sample id 0 under tau0_seed,
+// drawn by the 32-walker kernel; its parents and depths become p0 and level.
+void build_tau0_wilson(kc_graph *g, int &launches) {
+    GraphView gv = view_of(g);
+    Plan p;
+    p.BW = 1;
+    p.BT = 1;
+    ensure_ws(g, p);
+    Carved c = carve(g, p);
+    WaveView w = c.wv;
+    w.B = 1;
+    KC_CK(g, cudaMemsetAsync(g->d_err, 0, 2 * sizeof(uint32_t), g->stream));
+    KC_CK(g, launch_iota(c.sids, 0, 1, g->stream));
+    KC_CK(g, launch_wave_init(gv, w, g->stream));
+    KC_CK(g, launch_wilson_warp(gv, w, g->cfg.tau0_seed, c.sids, g->d_sorder, step_cap_of(g),
+                                g->stream));
+    int32_t *d_cnt = (int32_t *)g->d_scratch;  // [0] deepest, [1] outside the tree
+    KC_CK(g, cudaMemsetAsync(d_cnt, 0, 2 * sizeof(int32_t), g->stream));
+    KC_CK(g, launch_tau0_from_words(g->n, w.word, g->d_p0, g->d_level0, d_cnt, d_cnt + 1,
+                                    g->stream));
+    launches += 4;
+    uint32_t hdr[2] = {0, 0};
+    KC_CK(g, copy_sync(g, hdr, g->d_err, sizeof(hdr), cudaMemcpyDeviceToHost));
+    if (hdr[0] & kErrStepLimit) {
+        g->last_error = "the Wilson path tree exceeded the step cap";
+        throw Fail{KC_ERR_STEP_LIMIT};
+    }
+    if (hdr[0]) throw Fail{KC_ERR_CUDA};
+    int32_t h[2] = {0, 0};
+    KC_CK(g, copy_sync(g, h, d_cnt, sizeof(h), cudaMemcpyDeviceToHost));
+    if (h[1]) throw Fail{KC_ERR_DISCONNECTED};
+    g->ecc = h[0];
+}
+
+void build_tau0(kc_graph *g, int &launches) {
+    if (g->cfg.tau0_kind == KC_TAU0_DFS) build_tau0_dfs(g, launches);
+    else if (g->cfg.tau0_kind == KC_TAU0_WILSON) build_tau0_wilson(g, launches);
+    else build_tau0_bfs(g, launches);
 }
 
 // DFN of tau0 with the same passes as the sampled trees (one tree).
@@ -1165,7 +1226,8 @@ kc_status kc_graph_create(int64_t n, const int64_t *row_off, const int32_t *col,
         cfg = *cfg_in;
     }
     if (cfg.walker < KC_WALK_AUTO || cfg.walker > KC_WALK_HYBRID ||
-        cfg.hybrid_prefix_permille < 0 || cfg.hybrid_tail_permille < 0)
+        cfg.hybrid_prefix_permille < 0 || cfg.hybrid_tail_permille < 0 ||
+        cfg.tau0_kind < KC_TAU0_BFS || cfg.tau0_kind > KC_TAU0_WILSON)
         return KC_ERR_INVALID_ARG;
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
@@ -1253,8 +1315,6 @@ kc_status kc_graph_create(int64_t n, const int64_t *row_off, const int32_t *col,
             if (cfg.root == -1) g->root = central_root(g, g->root, launches);
         }
         gv.root = g->root;
-        build_tau0(g, launches);
-        gv.ecc = g->ecc;
         // Start order of the concurrent walkers: a fixed pseudo-random
         // permutation (vertices sorted by a 32-bit mix of their id), so that the
         // 32 walkers of a tree start far apart and rarely block each other.  Any
@@ -1281,6 +1341,9 @@ kc_status kc_graph_create(int64_t n, const int64_t *row_off, const int32_t *col,
                                      cudaMemcpyHostToDevice, g->stream));
             KC_CK(g, cudaStreamSynchronize(g->stream));
         }
+        build_tau0(g, launches);
+        gv.ecc = g->ecc;
+
         // overflow margin: |f| <= 4 m^2 ecc (Theorem 5's proof) must stay below 2^62
         {
             const long double bound = 4.0L * (long double)g->m * (long double)g->m * (long double)g->ecc;
@@ -1613,6 +1676,11 @@ kc_status kc_reset_timers(kc_graph *g) {
 kc_status kc_update(kc_graph *g, const kc_edge_op *ops, int64_t n_ops, int32_t mode) {
     if (!g || (n_ops > 0 && !ops) || n_ops < 0) return KC_ERR_INVALID_ARG;
     if (mode != KC_UPDATE_BSM && mode != KC_UPDATE_ISM) return KC_ERR_INVALID_ARG;
+    if (g->cfg.tau0_kind != KC_TAU0_BFS) {
+        g->last_error = "kc_update: sample maintenance rebuilds tau0 as a BFS tree; "
+                        "create the handle with tau0_kind = KC_TAU0_BFS";
+        return KC_ERR_INVALID_ARG;
+    }
     if (!g->cfg.keep_trees) return KC_ERR_NOT_RETAINED;
     if (g->pool == 0) return KC_ERR_NO_SAMPLES;
     if (n_ops == 0) return KC_OK;

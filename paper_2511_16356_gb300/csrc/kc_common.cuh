@@ -254,6 +254,11 @@ cudaError_t launch_build_records(const GraphView &g, VRec *rec, int32_t *deg, cu
 cudaError_t launch_validate(const GraphView &g, uint32_t *flags, cudaStream_t s);
 cudaError_t launch_root(const GraphView &g, unsigned long long *best, cudaStream_t s);
 cudaError_t launch_bfs_init(int64_t n, int32_t r, int32_t *level, cudaStream_t s);
+cudaError_t launch_dfs_tree(const GraphView &g, int32_t r, int32_t *p0, int32_t *level,
+                            int32_t *sv, int64_t *se, int32_t *deepest, int32_t *unreached,
+                            cudaStream_t s);
+cudaError_t launch_tau0_from_words(int64_t n, const uint64_t *word, int32_t *p0, int32_t *level,
+                                   int32_t *deepest, int32_t *outside, cudaStream_t s);
 cudaError_t launch_argmax_score(int64_t n, const int32_t *la, const int32_t *lb, int mode,
                                 unsigned long long *best, cudaStream_t s);
 cudaError_t launch_central_pick(int64_t n, const int32_t *deg, int32_t dmax, const int32_t *la,

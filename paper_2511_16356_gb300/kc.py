@@ -28,6 +28,7 @@ KC_STOP_CLT, KC_STOP_HOEFFDING = 0, 1
 KC_UPDATE_BSM, KC_UPDATE_ISM = 0, 1
 KC_R_CG, KC_R_GIVEN = 0, 1
 KC_WALK_AUTO, KC_WALK_LANE, KC_WALK_WARP, KC_WALK_HYBRID = 0, 1, 2, 3
+KC_TAU0_BFS, KC_TAU0_DFS, KC_TAU0_WILSON = 0, 1, 2
 KC_OP_INSERT, KC_OP_DELETE = 0, 1
 
 
@@ -42,6 +43,8 @@ class kc_config(ctypes.Structure):
         ("max_trees", ctypes.c_int64), ("step_cap", ctypes.c_int64),
         ("mem_fraction", ctypes.c_double), ("sample_id_base", ctypes.c_int64),
         ("hybrid_prefix_permille", ctypes.c_int32), ("hybrid_tail_permille", ctypes.c_int32),
+        ("tau0_kind", ctypes.c_int32), ("reserved1", ctypes.c_int32),
+        ("tau0_seed", ctypes.c_uint64),
     ]
 
 

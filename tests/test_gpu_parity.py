@@ -272,3 +272,26 @@ def test_pipelined_chunks_bit_exact(name):
         f_ref, st_ref = O.sample_batch(g, t0, 31, 0, 120)
         assert np.array_equal(got["steps"], st_ref)
         assert np.array_equal(got["f"], f_ref)
+
+
+@pytest.mark.parametrize("kind,kname", [(kc.KC_TAU0_DFS, "dfs"), (kc.KC_TAU0_WILSON, "wilson")])
+@pytest.mark.parametrize("name", ["er300", "grid17x13", "K3,5", "cl3000"])
+def test_dfs_and_wilson_path_trees_bit_exact(name, kind, kname):
+    """Exp-II path selections: tau0 built on the device as the depth-first tree
+    or as the Wilson tree of sample id 0 under tau0_seed equals the oracle's,
+    and so do the sampled trees' f and step counts."""
+    g = SMALL[name]()
+    t0 = O.tau0(g, kind=kname, seed=77)
+    with kc.KemenyGraph.from_graph(g, _cfg(tau0_kind=kind, tau0_seed=77)) as G:
+        tau = G.tau0()
+        assert tau["root"] == t0.r and tau["ecc"] == t0.ecc
+        assert np.array_equal(tau["p0"], t0.p0)
+        assert np.array_equal(tau["level"], t0.level)
+        assert np.array_equal(tau["in0"], t0.in0) and np.array_equal(tau["out0"], t0.out0)
+        G.sample(5, 64)
+        got = G.samples()
+        f_ref, st_ref = O.sample_batch(g, t0, 5, 0, 64)
+        assert np.array_equal(got["steps"], st_ref)
+        assert np.array_equal(got["f"], f_ref)
+        assert kc.STATUS[kc.kc_update(G.h, [(0, 1, 1)], kc.KC_UPDATE_ISM, check=False)] == \
+            "KC_ERR_INVALID_ARG"
