@@ -219,7 +219,6 @@ enum : int {
     pIdle = 0,     // needs a start vertex
     pWalk = 1,     // owns frontier c and departs from it
     pWait = 2,     // arrow (or empty path) points at x, owned by another lane
-    pArrive = 3,   // unused (the re-departure vertex's word and record are kept)
     pPopSet = 4,   // read the re-departure vertex before freeing a popped segment
     pPop = 5,      // free the vertices pcur .. pend of a popped cycle
     pCount = 6,    // length of the committed path
