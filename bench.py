@@ -205,6 +205,40 @@ def serve_workload(n_graphs: int, n_max: int, seed: int = 3):
     return gs
 
 
+def batched_leg(args, kc):
+    """Many small graphs: one kc_sample_multi call (all walks in one launch)
+    against one kc_sample call per graph, same trees."""
+    gs = serve_workload(args.serve_graphs, args.serve_nmax)
+    T = args.batched_trees
+    cfg = kc.kc_config_default()
+    cfg.keep_trees = 0
+
+    def run(batched):
+        hs = [kc.KemenyGraph.from_graph(g, cfg) for g in gs]
+        kc.kc_sample_multi([h.h for h in hs], [1] * len(hs), [8] * len(hs))  # warm-up
+        import torch
+
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        if batched:
+            kc.kc_sample_multi([h.h for h in hs], [1] * len(hs), [T] * len(hs))
+        else:
+            for h in hs:
+                h.sample(1, T)
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t
+        f = [h.samples()["f"] for h in hs]
+        for h in hs:
+            h.close()
+        return len(gs) * T / el, f
+
+    v_b, f_b = run(True)
+    v_s, f_s = run(False)
+    return {"workload": f"{len(gs)} graphs of the serving mix, {T} trees each",
+            "batched_trees_per_s": v_b, "separate_calls_trees_per_s": v_s,
+            "identical_results": all(np.array_equal(a, b) for a, b in zip(f_b, f_s))}
+
+
 def serve_leg(args, kc):
     """Served (continuous batching, `--serve-workers` streams) against the plain
     one-graph-per-call path on the same Poisson stream of Kemeny queries."""
@@ -319,6 +353,8 @@ def main():
     ap.add_argument("--serve-nmax", type=float, default=3e4)
     ap.add_argument("--serve-queries", type=int, default=96)
     ap.add_argument("--serve-workers", type=int, default=8)
+    ap.add_argument("--batched-trees", type=int, default=256,
+                    help="trees per graph in the batched multi-graph leg")
     ap.add_argument("--serve-load", type=float, default=1.5,
                     help="offered query rate as a multiple of the plain path's capacity")
     args = ap.parse_args()
@@ -490,6 +526,7 @@ def main():
     # ---- served p50/p99 against the plain path (rank 0)
     if not args.no_serve and rank == 0:
         out["serve"] = serve_leg(args, kc)
+        out["batched"] = batched_leg(args, kc)
 
     # ---- the CPU oracle on the host cores (rank 0, N = 1 only)
     if not args.no_cpu_baseline and rank == 0 and ws == 1:

@@ -194,6 +194,17 @@ kc_status kc_graph_reset(kc_graph *g, uint64_t seed, int64_t sample_id_base);
 kc_status kc_sample(kc_graph *g, uint64_t seed, int64_t n_trees);
 
 /*
+ * Batched multi-graph sampling (no counterpart in the paper): the same result
+ * as kc_sample(graphs[i], seeds[i], n_trees[i]) for every i, but the walks of
+ * all graphs run in one 32-walker launch per round (one warp per tree, graphs
+ * of uneven size mixed), which fills the GPU when each graph alone has too few
+ * trees.  All work runs on graphs[0]'s stream.  The handles must be distinct
+ * and on one device.  Errors: as kc_sample; on error no pool changes.
+ */
+kc_status kc_sample_multi(kc_graph *const *graphs, const uint64_t *seeds, const int64_t *n_trees,
+                          int32_t count);
+
+/*
  * Kemeny constant estimate K_hat = sum w f / (2m sum w) over the pool,
  * sampling more trees first (with the handle's seed, or 0 if none was set)
  * until the stopping rule for relative error eps at failure probability delta

@@ -233,21 +233,49 @@ enum : int {
 // One warp per block: a block frees its SM slot as soon as its own tree is
 // done (tree times vary several-fold on long-diameter graphs, and a 4-warp
 // block would hold three finished warps' registers until its slowest tree).
+// kMulti: block j walks tree mw.entry[j].y of graph mw.entry[j].x, every graph
+// with its own view, wave, seed, sample ids, start order and step cap (the
+// batched multi-graph launch); otherwise one graph and wave as passed.
 constexpr int kWarpWalkerBlock = 32;
-__global__ void __launch_bounds__(kWarpWalkerBlock, 24) k_wilson_warp(GraphView g, WaveView w, uint64_t seed,
-                                                     const int64_t *__restrict__ sids,
-                                                     const int32_t *__restrict__ sorder,
-                                                     int64_t step_cap, int64_t iter_cap,
-                                                     const int32_t *__restrict__ rs_q,
-                                                     const int32_t *__restrict__ rs_pos,
-                                                     volatile int32_t *done_flag) {
+template <bool kMulti>
+__global__ void __launch_bounds__(kWarpWalkerBlock, 24)
+    k_wilson_warp(GraphView g_in, WaveView w_in, uint64_t seed_in,
+                  const int64_t *__restrict__ sids_in, const int32_t *__restrict__ sorder_in,
+                  int64_t step_cap_in, int64_t iter_cap_in, const int32_t *__restrict__ rs_q,
+                  const int32_t *__restrict__ rs_pos, volatile int32_t *done_flag, MultiWalk mw) {
     const unsigned kFull = 0xFFFFFFFFu;
     const int lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
     __shared__ int32_t xs[32];  // vertex each cycle lane's predecessor waits on
-    const int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (t >= w.B) return;                   // whole warp
-    if (rs_q && rs_q[t] < 0) return;        // whole warp: finished by the lane walker
+    GraphView g;
+    WaveView w;
+    uint64_t seed;
+    const int64_t *sids;
+    const int32_t *sorder;
+    int64_t step_cap, iter_cap, t;
+    if constexpr (kMulti) {
+        if ((int64_t)blockIdx.x >= mw.count) return;
+        const int2 e = mw.entry[blockIdx.x];
+        g = mw.graphs[e.x];
+        w = mw.waves[e.x];
+        seed = mw.seeds[e.x];
+        sids = mw.sids[e.x];
+        sorder = mw.sorders[e.x];
+        step_cap = mw.step_caps[e.x];
+        iter_cap = 4 * step_cap + 64 * g.n + 4096;
+        t = e.y;
+    } else {
+        g = g_in;
+        w = w_in;
+        seed = seed_in;
+        sids = sids_in;
+        sorder = sorder_in;
+        step_cap = step_cap_in;
+        iter_cap = iter_cap_in;
+        t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+        if (t >= w.B) return;               // whole warp
+        if (rs_q && rs_q[t] < 0) return;    // whole warp: finished by the lane walker
+    }
     const int64_t n = g.n;
     uint64_t *word = w.word + t * n;
     int32_t *ord = w.ord + t * n;
@@ -491,8 +519,15 @@ cudaError_t launch_wilson_warp(const GraphView &g, WaveView w, uint64_t seed, co
     // a correct run needs at most about 3 iterations per departure (walk,
     // count, commit / pop), however the walkers serialise
     const int64_t iter_cap = 4 * step_cap + 64 * g.n + 4096;
-    k_wilson_warp<<<(unsigned)w.B, kWarpWalkerBlock, 0, s>>>(
-        g, w, seed, sids, sorder, step_cap, iter_cap, rs_q, rs_pos, done_flag);
+    k_wilson_warp<false><<<(unsigned)w.B, kWarpWalkerBlock, 0, s>>>(
+        g, w, seed, sids, sorder, step_cap, iter_cap, rs_q, rs_pos, done_flag, MultiWalk{});
+    return cudaGetLastError();
+}
+
+cudaError_t launch_wilson_warp_multi(const MultiWalk &mw, cudaStream_t s) {
+    if (mw.count <= 0) return cudaSuccess;
+    k_wilson_warp<true><<<(unsigned)mw.count, kWarpWalkerBlock, 0, s>>>(
+        GraphView{}, WaveView{}, 0, nullptr, nullptr, 0, 0, nullptr, nullptr, nullptr, mw);
     return cudaGetLastError();
 }
 

@@ -465,7 +465,9 @@ void run_wave_pipelined(kc_graph *g, Plan &p, int64_t B, int64_t sid0) {
 }
 
 void run_wave(kc_graph *g, Plan &p, int64_t B, int64_t sid0, bool canonical = false) {
-    if (!canonical && g->walker == KC_WALK_WARP && B > 1) {
+    // pipelining pays when traversal and TTF take long enough to hide: several
+    // sub-waves, or large graphs; short waves of small graphs run straight
+    if (!canonical && g->walker == KC_WALK_WARP && B > 1 && (B > p.BT || g->n >= (1 << 16))) {
         try {
             run_wave_pipelined(g, p, B, sid0);
         } catch (Fail &) {
@@ -1131,6 +1133,156 @@ void do_sample(kc_graph *g, int64_t ntrees) {
     g->next_sid = sid_base + ntrees;
 }
 
+// Batched multi-graph sampling: the walks of every graph's wave run in one
+// 32-walker launch (one warp per tree, graphs mixed), then each graph's
+// traversal, TTF and pool append.  All work goes to the first graph's stream.
+void do_sample_multi(kc_graph *const *gs, const int64_t *n_trees, int32_t count) {
+    cudaStream_t s0 = gs[0]->stream;
+    std::vector<cudaStream_t> saved((size_t)count);
+    std::vector<int64_t> pool0((size_t)count), sid0((size_t)count), left((size_t)count);
+    std::vector<Plan> plans((size_t)count);
+    for (int32_t i = 0; i < count; ++i) {
+        kc_graph *g = gs[i];
+        saved[(size_t)i] = g->stream;
+        g->stream = s0;
+        pool0[(size_t)i] = g->pool;
+        sid0[(size_t)i] = g->next_sid;
+        left[(size_t)i] = n_trees[i];
+    }
+    void *d_tab = nullptr;
+    try {
+        for (int32_t i = 0; i < count; ++i) {
+            kc_graph *g = gs[i];
+            if (n_trees[i] <= 0) continue;
+            ensure_pool(g, g->pool + n_trees[i]);
+            plans[(size_t)i] = plan_for(g, n_trees[i], false);
+            ensure_ws(g, plans[(size_t)i]);
+        }
+        for (;;) {
+            // this round: up to one wave per graph
+            std::vector<GraphView> gv;
+            std::vector<WaveView> wv;
+            std::vector<uint64_t> seeds;
+            std::vector<const int64_t *> sids;
+            std::vector<const int32_t *> sorders;
+            std::vector<int64_t> caps;
+            std::vector<int32_t> idx;  // graph of each table row
+            std::vector<int64_t> bs;
+            for (int32_t i = 0; i < count; ++i) {
+                kc_graph *g = gs[i];
+                if (left[(size_t)i] <= 0) continue;
+                const int64_t B = std::min<int64_t>(left[(size_t)i], plans[(size_t)i].BW);
+                Carved c = carve(g, plans[(size_t)i]);
+                WaveView w = c.wv;
+                w.B = B;
+                const GraphView v = view_of(g);
+                KC_CK(g, cudaMemsetAsync(g->d_err, 0, 2 * sizeof(uint32_t), s0));
+                KC_CK(g, launch_iota(c.sids, g->next_sid, B, s0));
+                KC_CK(g, launch_wave_init(v, w, s0));
+                gv.push_back(v);
+                wv.push_back(w);
+                seeds.push_back(g->seed);
+                sids.push_back(c.sids);
+                sorders.push_back(g->d_sorder);
+                caps.push_back(step_cap_of(g));
+                idx.push_back(i);
+                bs.push_back(B);
+            }
+            if (idx.empty()) break;
+            const size_t G = idx.size();
+            // trees of different graphs interleaved, so a launch mixes sizes
+            std::vector<int2> entry;
+            int64_t most = 0;
+            for (int64_t b : bs) most = std::max(most, b);
+            for (int64_t t = 0; t < most; ++t)
+                for (size_t k = 0; k < G; ++k)
+                    if (t < bs[k]) entry.push_back(make_int2((int)k, (int)t));
+            const size_t bytes = sizeof(GraphView) * G + sizeof(WaveView) * G + 8 * G * 4 +
+                                 sizeof(int2) * entry.size() + 256 * 8;
+            kc_graph *g0 = gs[0];
+            KC_CK(g0, cudaMallocAsync(&d_tab, bytes, s0));
+            char *base = (char *)d_tab;
+            size_t off = 0;
+            auto put = [&](const void *src, size_t nb) {
+                void *dst = base + off;
+                KC_CK(g0, cudaMemcpyAsync(dst, src, nb, cudaMemcpyHostToDevice, s0));
+                off += (nb + 255) & ~size_t(255);
+                return dst;
+            };
+            MultiWalk mw;
+            mw.graphs = (const GraphView *)put(gv.data(), sizeof(GraphView) * G);
+            mw.waves = (const WaveView *)put(wv.data(), sizeof(WaveView) * G);
+            mw.seeds = (const uint64_t *)put(seeds.data(), 8 * G);
+            mw.sids = (const int64_t *const *)put(sids.data(), 8 * G);
+            mw.sorders = (const int32_t *const *)put(sorders.data(), 8 * G);
+            mw.step_caps = (const int64_t *)put(caps.data(), 8 * G);
+            mw.entry = (const int2 *)put(entry.data(), sizeof(int2) * entry.size());
+            mw.count = (int64_t)entry.size();
+            {
+                Phase ph(g0, g0->t_wilson);
+                KC_CK(g0, launch_wilson_warp_multi(mw, s0));
+                ph.done(1);
+            }
+            KC_CK(g0, cudaFreeAsync(d_tab, s0));
+            d_tab = nullptr;
+            // per graph: errors, traversal, TTF, pool append
+            for (size_t k = 0; k < G; ++k) {
+                const int32_t i = idx[k];
+                kc_graph *g = gs[i];
+                Plan &p = plans[(size_t)i];
+                const int64_t B = bs[k];
+                uint32_t hdr[2] = {0, 0};
+                KC_CK(g, copy_sync(g, hdr, g->d_err, sizeof(hdr), cudaMemcpyDeviceToHost));
+                if (hdr[0] & kErrStepLimit) {
+                    g->last_error = "Wilson walk exceeded the step cap";
+                    throw Fail{KC_ERR_STEP_LIMIT};
+                }
+                if (hdr[0]) throw Fail{KC_ERR_CUDA};
+                if (p.bit) ensure_stack(g, p, hdr[1]);
+                Carved c = carve(g, p);
+                WaveView w = c.wv;
+                w.B = B;
+                const GraphView v = view_of(g);
+                for (int64_t sub = 0; sub < B; sub += p.BT) {
+                    const int64_t b = std::min<int64_t>(p.BT, B - sub);
+                    WaveView sw = w;
+                    sw.B = b;
+                    sw.word = w.word + sub * g->n;
+                    sw.ord = w.ord + sub * g->n;
+                    sw.steps = w.steps + sub;
+                    sw.f = w.f + sub;
+                    int nl = 0;
+                    KC_CK(g, launch_traverse(v, sw, p.bit, s0, &nl, fast_traversal(g)));
+                    if (p.bit) KC_CK(g, launch_ttf_bit(v, sw, s0));
+                    else KC_CK(g, launch_ttf_scan(v, sw, s0));
+                    g->t_traverse.launches += nl;
+                    g->t_ttf.launches += 1;
+                }
+                KC_CK(g, launch_pool_append(w, g->pool, g->d_f, g->d_w, g->d_steps, g->d_sid,
+                                            c.sids, g->cfg.keep_trees ? g->d_parents : nullptr,
+                                            g->n, s0));
+                KC_CK(g, copy_sync(g, hdr, g->d_err, sizeof(hdr), cudaMemcpyDeviceToHost));
+                if (hdr[0]) throw Fail{KC_ERR_CUDA};
+                for (int64_t q = 0; q < B; ++q) g->h_modified[(size_t)(g->pool + q)] = 0;
+                g->pool += B;
+                g->next_sid += B;
+                g->last_wave = B;
+                left[(size_t)i] -= B;
+            }
+        }
+    } catch (Fail &) {
+        if (d_tab) cudaFreeAsync(d_tab, s0);
+        cudaStreamSynchronize(s0);
+        for (int32_t i = 0; i < count; ++i) {
+            gs[i]->pool = pool0[(size_t)i];
+            gs[i]->next_sid = sid0[(size_t)i];
+            gs[i]->stream = saved[(size_t)i];
+        }
+        throw;
+    }
+    for (int32_t i = 0; i < count; ++i) gs[i]->stream = saved[(size_t)i];
+}
+
 }  // namespace
 
 // =========================================================================
@@ -1425,6 +1577,36 @@ kc_status kc_sample(kc_graph *g, uint64_t seed, int64_t n_trees) {
         do_sample(g, n_trees);
     } catch (Fail &f) {
         g->seeded = was_seeded;
+        return f.st;
+    }
+    return KC_OK;
+}
+
+kc_status kc_sample_multi(kc_graph *const *graphs, const uint64_t *seeds, const int64_t *n_trees,
+                          int32_t count) {
+    if (!graphs || !seeds || !n_trees || count <= 0) return KC_ERR_INVALID_ARG;
+    for (int32_t i = 0; i < count; ++i) {
+        kc_graph *g = graphs[i];
+        if (!g || n_trees[i] < 0) return KC_ERR_INVALID_ARG;
+        for (int32_t j = 0; j < i; ++j)
+            if (graphs[j] == g) return KC_ERR_INVALID_ARG;
+        if (g->device != graphs[0]->device) return KC_ERR_INVALID_ARG;
+        if (g->seeded && seeds[i] != g->seed) {
+            g->last_error = "kc_sample_multi: the handle is already seeded with a different seed";
+            return KC_ERR_INVALID_ARG;
+        }
+        if (g->next_sid + n_trees[i] > ((int64_t)1 << 32)) return KC_ERR_INVALID_ARG;
+    }
+    std::vector<char> was((size_t)count);
+    for (int32_t i = 0; i < count; ++i) {
+        was[(size_t)i] = graphs[i]->seeded;
+        graphs[i]->seed = seeds[i];
+        graphs[i]->seeded = true;
+    }
+    try {
+        do_sample_multi(graphs, n_trees, count);
+    } catch (Fail &f) {
+        for (int32_t i = 0; i < count; ++i) graphs[i]->seeded = was[(size_t)i];
         return f.st;
     }
     return KC_OK;

@@ -274,6 +274,19 @@ cudaError_t launch_level_order(int64_t n, int32_t ecc, const int32_t *level, int
                                int32_t *ord, cudaStream_t s);
 
 cudaError_t launch_wave_init(const GraphView &g, WaveView w, cudaStream_t s);
+// Batched multi-graph walk: device tables indexed by graph, one entry
+// (graph, tree of its wave) per warp.
+struct MultiWalk {
+    const GraphView *graphs = nullptr;
+    const WaveView *waves = nullptr;
+    const uint64_t *seeds = nullptr;
+    const int64_t *const *sids = nullptr;
+    const int32_t *const *sorders = nullptr;
+    const int64_t *step_caps = nullptr;
+    const int2 *entry = nullptr;
+    int64_t count = 0;
+};
+cudaError_t launch_wilson_warp_multi(const MultiWalk &mw, cudaStream_t s);
 cudaError_t launch_wilson(const GraphView &g, WaveView w, uint64_t seed, const int64_t *sids,
                           int64_t step_cap, cudaStream_t s, const int32_t *sorder = nullptr,
                           int32_t *rs_q = nullptr, int32_t *rs_pos = nullptr,

@@ -42,8 +42,8 @@ struct kc_server {
     kc_server_config cfg{};
     int device = 0;
     std::chrono::steady_clock::time_point t0;
-    std::vector<Graph> graphs;
-    std::vector<std::unique_ptr<Request>> reqs;  // by ticket
+    std::deque<Graph> graphs;                    // stable addresses while graphs are added
+    std::vector<std::unique_ptr<Request>> reqs;  // by ticket (read under the lock)
     std::deque<int64_t> queue;                   // waiting tickets, submission order
     int64_t reserved = 0;                        // bytes reserved by running requests
     int64_t outstanding = 0;                     // submitted and not yet done
@@ -90,15 +90,19 @@ struct kc_server {
         cudaSetDevice(device);
         for (;;) {
             int64_t ticket = -1, bytes = 0;
+            Request *rp = nullptr;
+            Graph *gp = nullptr;
             {
                 std::unique_lock<std::mutex> lk(mu);
                 cv_work.wait(lk, [&] { return stop || (!queue.empty() && pick(&ticket, &bytes)); });
                 if (ticket < 0) return;  // stop requested and nothing admissible
-                graphs[(size_t)reqs[(size_t)ticket]->graph].busy = true;
+                rp = reqs[(size_t)ticket].get();
+                gp = &graphs[(size_t)rp->graph];
+                gp->busy = true;
                 reserved += bytes;
             }
-            Request &r = *reqs[(size_t)ticket];
-            Graph &g = graphs[(size_t)r.graph];
+            Request &r = *rp;
+            Graph &g = *gp;
             r.info.t_start_ms = now_ms();
             r.info.worker = wid;
             r.info.workspace_bytes = bytes;

@@ -110,6 +110,8 @@ _SIGS = {
     "kc_graph_release_workspace": (ctypes.c_int, [_P]),
     "kc_graph_reset": (ctypes.c_int, [_P, ctypes.c_uint64, ctypes.c_int64]),
     "kc_sample": (ctypes.c_int, [_P, ctypes.c_uint64, ctypes.c_int64]),
+    "kc_sample_multi": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.POINTER(ctypes.c_uint64),
+                                       ctypes.POINTER(ctypes.c_int64), ctypes.c_int32]),
     "kc_estimate": (ctypes.c_int, [_P, ctypes.c_double, ctypes.c_double,
                                    ctypes.POINTER(ctypes.c_double)]),
     "kc_update": (ctypes.c_int, [_P, ctypes.POINTER(kc_edge_op), ctypes.c_int64, ctypes.c_int32]),
@@ -221,6 +223,17 @@ def kc_sample(g, seed: int, n_trees: int, check: bool = True) -> int:
     st = load().kc_sample(g, seed, n_trees)
     if check:
         _check(st, "kc_sample", g)
+    return st
+
+
+def kc_sample_multi(handles, seeds, n_trees, check: bool = True) -> int:
+    k = len(handles)
+    hs = (_P * k)(*[h.value if isinstance(h, _P) else h for h in handles])
+    ss = (ctypes.c_uint64 * k)(*[int(x) for x in seeds])
+    ns = (ctypes.c_int64 * k)(*[int(x) for x in n_trees])
+    st = load().kc_sample_multi(hs, ss, ns, k)
+    if check:
+        _check(st, "kc_sample_multi")
     return st
 
 

@@ -295,3 +295,30 @@ def test_dfs_and_wilson_path_trees_bit_exact(name, kind, kname):
         assert np.array_equal(got["f"], f_ref)
         assert kc.STATUS[kc.kc_update(G.h, [(0, 1, 1)], kc.KC_UPDATE_ISM, check=False)] == \
             "KC_ERR_INVALID_ARG"
+
+
+def test_sample_multi_equals_separate_calls_and_oracle():
+    """One batched walker launch over graphs of uneven size and both TTF
+    variants: every graph's pool equals the oracle's, as with kc_sample."""
+    names = ["er300", "grid17x13", "K7", "path33", "cl3000", "star9"]
+    gs = [SMALL[k]() for k in names]
+    seeds = [3 + i for i in range(len(gs))]
+    counts = [50, 37, 64, 10, 80, 1]
+    Gs = [kc.KemenyGraph.from_graph(g, _cfg()) for g in gs]
+    try:
+        kc.kc_sample_multi([G.h for G in Gs], seeds, counts)
+        kc.kc_sample_multi([G.h for G in Gs], seeds, [5] * len(gs))  # a second call appends
+        for g, G, sd, k in zip(gs, Gs, seeds, counts):
+            t0 = O.tau0(g)
+            got = G.samples()
+            assert np.array_equal(got["sid"], np.arange(k + 5))
+            f_ref, st_ref = O.sample_batch(g, t0, sd, 0, k + 5)
+            assert np.array_equal(got["steps"], st_ref)
+            assert np.array_equal(got["f"], f_ref)
+        # a seed that differs from a handle's fixed seed is refused and changes nothing
+        st = kc.kc_sample_multi([G.h for G in Gs], [99] * len(gs), [4] * len(gs), check=False)
+        assert kc.STATUS[st] == "KC_ERR_INVALID_ARG"
+        assert Gs[0].stats()["pool_trees"] == counts[0] + 5
+    finally:
+        for G in Gs:
+            G.close()
