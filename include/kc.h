@@ -194,6 +194,14 @@ kc_status kc_graph_reset(kc_graph *g, uint64_t seed, int64_t sample_id_base);
 kc_status kc_sample(kc_graph *g, uint64_t seed, int64_t n_trees);
 
 /*
+ * Reserve device memory ahead of sampling (no counterpart in the paper): pool
+ * capacity for n_trees more trees and the workspace of a wave of n_trees, so
+ * that later kc_sample calls allocate nothing.  Errors: INVALID_ARG,
+ * OUT_OF_MEMORY, CUDA.
+ */
+kc_status kc_reserve(kc_graph *g, int64_t n_trees);
+
+/*
  * Batched multi-graph sampling (no counterpart in the paper): the same result
  * as kc_sample(graphs[i], seeds[i], n_trees[i]) for every i, but the walks of
  * all graphs run in one 32-walker launch per round (one warp per tree, graphs

@@ -173,10 +173,16 @@ __global__ void k_leaf_up(GraphView g, WaveView w) {
 // order inside a chunk.  A child's offset is what an atomic add of its
 // group's sizes to the parent's size returns (parent in a later chunk), or the
 // parent's size at the chunk start plus the in-chunk siblings at lower lanes.
-__global__ void __launch_bounds__(128) k_bottom_up_offsets(GraphView g, WaveView w) {
+template <bool kMulti>
+__global__ void __launch_bounds__(128) k_bottom_up_offsets(GraphView g_in, WaveView w_in,
+                                                           MultiSub ms) {
     const int lane = threadIdx.x & 31;
-    const int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (t >= w.B) return;
+    GraphView g;
+    WaveView w;
+    int64_t t;
+    if (!pick_tree<kMulti>(ms, g_in, w_in, ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5,
+                           g, w, t))
+        return;
     const int64_t n = g.n;
     const int32_t *__restrict__ ord = w.ord + wave_tree(w, t) * n;
     const uint64_t *__restrict__ word = w.word + wave_tree(w, t) * n;
@@ -267,10 +273,17 @@ __global__ void __launch_bounds__(128) k_sibling_offsets(GraphView g, WaveView w
     }
 }
 
-__global__ void __launch_bounds__(128) k_top_down(GraphView g, WaveView w, int want_pre) {
+template <bool kMulti>
+__global__ void __launch_bounds__(128) k_top_down(GraphView g_in, WaveView w_in, int want_pre_in,
+                                                  MultiSub ms) {
     const int lane = threadIdx.x & 31;
-    const int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (t >= w.B) return;
+    GraphView g;
+    WaveView w;
+    int64_t t;
+    if (!pick_tree<kMulti>(ms, g_in, w_in, ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5,
+                           g, w, t))
+        return;
+    const int want_pre = kMulti ? (w.bit != nullptr) : want_pre_in;
     const int64_t n = g.n;
     const int32_t *__restrict__ ord = w.ord + wave_tree(w, t) * n;
     const uint64_t *__restrict__ word = w.word + wave_tree(w, t) * n;
@@ -339,7 +352,7 @@ cudaError_t launch_traverse(const GraphView &g, WaveView w, bool want_preorder, 
     if (mode == kTravChunked) {
         if ((e = cudaMemsetAsync(w.size, 0, sizeof(int32_t) * per, s)) != cudaSuccess) return e;
         if ((e = cudaMemsetAsync(w.vol, 0, sizeof(int64_t) * per, s)) != cudaSuccess) return e;
-        k_bottom_up_offsets<<<blocks, 128, 0, s>>>(g, w);
+        k_bottom_up_offsets<false><<<blocks, 128, 0, s>>>(g, w, MultiSub{});
     } else if (canonical) {
         if ((e = cudaMemsetAsync(w.size, 0, sizeof(int32_t) * per, s)) != cudaSuccess) return e;
         if ((e = cudaMemsetAsync(w.vol, 0, sizeof(int64_t) * per, s)) != cudaSuccess) return e;
@@ -353,8 +366,16 @@ cudaError_t launch_traverse(const GraphView &g, WaveView w, bool want_preorder, 
         k_child_count<<<grid, 256, 0, s>>>(g, w);
         k_leaf_up<<<grid, 256, 0, s>>>(g, w);
     }
-    k_top_down<<<blocks, 128, 0, s>>>(g, w, want_preorder ? 1 : 0);
+    k_top_down<false><<<blocks, 128, 0, s>>>(g, w, want_preorder ? 1 : 0, MultiSub{});
     if (launches) *launches += canonical ? 3 : (mode == kTravChunked ? 2 : 4);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_traverse_multi(const MultiSub &ms, cudaStream_t s) {
+    if (ms.count <= 0) return cudaSuccess;
+    const unsigned blocks = (unsigned)((ms.count * 32 + 127) / 128);
+    k_bottom_up_offsets<true><<<blocks, 128, 0, s>>>(GraphView{}, WaveView{}, ms);
+    k_top_down<true><<<blocks, 128, 0, s>>>(GraphView{}, WaveView{}, 0, ms);
     return cudaGetLastError();
 }
 

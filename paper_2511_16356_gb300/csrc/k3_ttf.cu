@@ -18,6 +18,8 @@
 //        are loaded first, then the 32 visits are replayed in lane order with the
 //        stack held in registers, each range add both issued to the Fenwick array
 //        (integer atomics) and folded into the pending queries of later lanes.
+#include <algorithm>
+
 #include "kc_common.cuh"
 
 namespace kc {
@@ -26,8 +28,12 @@ namespace {
 
 constexpr unsigned kFull = 0xFFFFFFFFu;
 
-__global__ void __launch_bounds__(256) k_ttf_scan(GraphView g, WaveView w) {
-    const int64_t t = blockIdx.y;
+template <bool kMulti>
+__global__ void __launch_bounds__(256) k_ttf_scan(GraphView g_in, WaveView w_in, MultiSub ms) {
+    GraphView g;
+    WaveView w;
+    int64_t t;
+    if (!pick_tree<kMulti>(ms, g_in, w_in, blockIdx.y, g, w, t)) return;  // whole block
     const int64_t n = g.n;
     const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const uint64_t *__restrict__ word = w.word + wave_tree(w, t) * n;
@@ -89,10 +95,15 @@ __device__ __forceinline__ void bit_range_add(int64_t *bit, int64_t n, int lane,
     if ((int64_t)r + 2 <= n) bit_point_add(bit, n, lane, (int64_t)r + 2, -val);
 }
 
-__global__ void __launch_bounds__(128) k_ttf_bit(GraphView g, WaveView w) {
+template <bool kMulti>
+__global__ void __launch_bounds__(128) k_ttf_bit(GraphView g_in, WaveView w_in, MultiSub ms) {
     const int lane = threadIdx.x & 31;
-    const int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (t >= w.B) return;
+    GraphView g;
+    WaveView w;
+    int64_t t;
+    if (!pick_tree<kMulti>(ms, g_in, w_in, ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5,
+                           g, w, t))
+        return;
     const int64_t n = g.n;
     const int32_t r = g.root;
     const int32_t twom = (int32_t)g.twom;  // host guarantees 2m < 2^31 for this kernel
@@ -220,14 +231,32 @@ cudaError_t launch_ttf_scan(const GraphView &g, WaveView w, cudaStream_t s) {
         if (e != cudaSuccess) return e;
     }
     dim3 grid((unsigned)((g.n + 255) / 256), (unsigned)w.B);
-    k_ttf_scan<<<grid, 256, 0, s>>>(g, w);
+    k_ttf_scan<false><<<grid, 256, 0, s>>>(g, w, MultiSub{});
     return cudaGetLastError();
 }
 
 cudaError_t launch_ttf_bit(const GraphView &g, WaveView w, cudaStream_t s) {
     cudaError_t e = cudaMemsetAsync(w.bit, 0, sizeof(int64_t) * (size_t)(w.B * (g.n + 1)), s);
     if (e != cudaSuccess) return e;
-    k_ttf_bit<<<(unsigned)((w.B * 32 + 127) / 128), 128, 0, s>>>(g, w);
+    k_ttf_bit<false><<<(unsigned)((w.B * 32 + 127) / 128), 128, 0, s>>>(g, w, MultiSub{});
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ttf_scan_multi(const MultiSub &ms, int64_t max_n, cudaStream_t s) {
+    for (int64_t r0 = 0; r0 < ms.count; r0 += 65535) {  // grid rows: at most 65535
+        MultiSub part = ms;
+        part.entry = ms.entry + r0;
+        part.count = std::min<int64_t>(65535, ms.count - r0);
+        dim3 grid((unsigned)((max_n + 255) / 256), (unsigned)part.count);
+        k_ttf_scan<true><<<grid, 256, 0, s>>>(GraphView{}, WaveView{}, part);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ttf_bit_multi(const MultiSub &ms, cudaStream_t s) {
+    if (ms.count <= 0) return cudaSuccess;
+    k_ttf_bit<true><<<(unsigned)((ms.count * 32 + 127) / 128), 128, 0, s>>>(GraphView{},
+                                                                           WaveView{}, ms);
     return cudaGetLastError();
 }
 

@@ -177,8 +177,11 @@ void ensure_ws(kc_graph *g, const Plan &p) {
     if (g->d_ws) KC_CK(g, cudaFreeAsync(g->d_ws, g->stream));
     g->d_ws = nullptr;
     g->ws_bytes = 0;
-    KC_CK(g, cudaMallocAsync(&g->d_ws, need, g->stream));
-    g->ws_bytes = need;
+    // 1% slack: plans for nearly equal tree counts fill the budget slightly
+    // differently, and should not reallocate
+    const size_t cap = need + need / 100;
+    KC_CK(g, cudaMallocAsync(&g->d_ws, cap, g->stream));
+    g->ws_bytes = cap;
 }
 
 void release_ws(kc_graph *g) {
@@ -1225,7 +1228,14 @@ void do_sample_multi(kc_graph *const *gs, const int64_t *n_trees, int32_t count)
             }
             KC_CK(g0, cudaFreeAsync(d_tab, s0));
             d_tab = nullptr;
-            // per graph: errors, traversal, TTF, pool append
+            // per graph: walk errors, BIT stacks, sub-wave buffers zeroed; the
+            // graphs whose wave is one sub-wave get one batched traversal and TTF
+            // launch, the others their own launches
+            std::vector<Carved> cv(G);
+            std::vector<GraphView> tg;
+            std::vector<WaveView> tw;
+            std::vector<int2> e_all, e_scan, e_bit;
+            int64_t max_n = 0;
             for (size_t k = 0; k < G; ++k) {
                 const int32_t i = idx[k];
                 kc_graph *g = gs[i];
@@ -1239,10 +1249,34 @@ void do_sample_multi(kc_graph *const *gs, const int64_t *n_trees, int32_t count)
                 }
                 if (hdr[0]) throw Fail{KC_ERR_CUDA};
                 if (p.bit) ensure_stack(g, p, hdr[1]);
-                Carved c = carve(g, p);
-                WaveView w = c.wv;
+                cv[k] = carve(g, p);
+                WaveView w = cv[k].wv;
                 w.B = B;
                 const GraphView v = view_of(g);
+                if (B <= p.BT) {
+                    const size_t nb = (size_t)B * (size_t)g->n;
+                    KC_CK(g, cudaMemsetAsync(w.size, 0, sizeof(int32_t) * nb, s0));
+                    KC_CK(g, cudaMemsetAsync(w.vol, 0, sizeof(int64_t) * nb, s0));
+                    if (p.bit) {
+                        KC_CK(g, cudaMemsetAsync(w.bit, 0,
+                                                 sizeof(int64_t) * (size_t)B * (size_t)(g->n + 1),
+                                                 s0));
+                    } else {
+                        KC_CK(g, cudaMemsetAsync(w.f, 0, sizeof(int64_t) * (size_t)B, s0));
+                        w.bit = nullptr;
+                    }
+                    const int gk = (int)tg.size();
+                    tg.push_back(v);
+                    tw.push_back(w);
+                    for (int64_t t = 0; t < B; ++t) {
+                        e_all.push_back(make_int2(gk, (int)t));
+                        (p.bit ? e_bit : e_scan).push_back(make_int2(gk, (int)t));
+                    }
+                    max_n = std::max<int64_t>(max_n, g->n);
+                    g->t_traverse.launches += 2;
+                    g->t_ttf.launches += 1;
+                    continue;
+                }
                 for (int64_t sub = 0; sub < B; sub += p.BT) {
                     const int64_t b = std::min<int64_t>(p.BT, B - sub);
                     WaveView sw = w;
@@ -1258,9 +1292,47 @@ void do_sample_multi(kc_graph *const *gs, const int64_t *n_trees, int32_t count)
                     g->t_traverse.launches += nl;
                     g->t_ttf.launches += 1;
                 }
+            }
+            if (!tg.empty()) {
+                const size_t Gt = tg.size();
+                const size_t tb = sizeof(GraphView) * Gt + sizeof(WaveView) * Gt +
+                                  sizeof(int2) * (e_all.size() + e_scan.size() + e_bit.size()) +
+                                  256 * 6;
+                KC_CK(g0, cudaMallocAsync(&d_tab, tb, s0));
+                char *tbase = (char *)d_tab;
+                size_t toff = 0;
+                auto tput = [&](const void *src, size_t nb) {
+                    void *dst = tbase + toff;
+                    if (nb) KC_CK(g0, cudaMemcpyAsync(dst, src, nb, cudaMemcpyHostToDevice, s0));
+                    toff += (nb + 255) & ~size_t(255);
+                    return dst;
+                };
+                MultiSub ms;
+                ms.graphs = (const GraphView *)tput(tg.data(), sizeof(GraphView) * Gt);
+                ms.waves = (const WaveView *)tput(tw.data(), sizeof(WaveView) * Gt);
+                MultiSub m_all = ms, m_scan = ms, m_bit = ms;
+                m_all.entry = (const int2 *)tput(e_all.data(), sizeof(int2) * e_all.size());
+                m_all.count = (int64_t)e_all.size();
+                m_scan.entry = (const int2 *)tput(e_scan.data(), sizeof(int2) * e_scan.size());
+                m_scan.count = (int64_t)e_scan.size();
+                m_bit.entry = (const int2 *)tput(e_bit.data(), sizeof(int2) * e_bit.size());
+                m_bit.count = (int64_t)e_bit.size();
+                KC_CK(g0, launch_traverse_multi(m_all, s0));
+                KC_CK(g0, launch_ttf_scan_multi(m_scan, max_n, s0));
+                KC_CK(g0, launch_ttf_bit_multi(m_bit, s0));
+                KC_CK(g0, cudaFreeAsync(d_tab, s0));
+                d_tab = nullptr;
+            }
+            for (size_t k = 0; k < G; ++k) {
+                const int32_t i = idx[k];
+                kc_graph *g = gs[i];
+                const int64_t B = bs[k];
+                WaveView w = cv[k].wv;
+                w.B = B;
                 KC_CK(g, launch_pool_append(w, g->pool, g->d_f, g->d_w, g->d_steps, g->d_sid,
-                                            c.sids, g->cfg.keep_trees ? g->d_parents : nullptr,
+                                            cv[k].sids, g->cfg.keep_trees ? g->d_parents : nullptr,
                                             g->n, s0));
+                uint32_t hdr[2] = {0, 0};
                 KC_CK(g, copy_sync(g, hdr, g->d_err, sizeof(hdr), cudaMemcpyDeviceToHost));
                 if (hdr[0]) throw Fail{KC_ERR_CUDA};
                 for (int64_t q = 0; q < B; ++q) g->h_modified[(size_t)(g->pool + q)] = 0;
@@ -1577,6 +1649,21 @@ kc_status kc_sample(kc_graph *g, uint64_t seed, int64_t n_trees) {
         do_sample(g, n_trees);
     } catch (Fail &f) {
         g->seeded = was_seeded;
+        return f.st;
+    }
+    return KC_OK;
+}
+
+kc_status kc_reserve(kc_graph *g, int64_t n_trees) {
+    if (!g || n_trees < 0) return KC_ERR_INVALID_ARG;
+    if (n_trees == 0) return KC_OK;
+    try {
+        ensure_pool(g, g->pool + n_trees);
+        Plan p = plan_for(g, n_trees, false);
+        ensure_ws(g, p);
+        if (g->walker == KC_WALK_WARP) ensure_pipeline(g, p.BW);
+        KC_CK(g, cudaStreamSynchronize(g->stream));
+    } catch (Fail &f) {
         return f.st;
     }
     return KC_OK;

@@ -287,6 +287,42 @@ struct MultiWalk {
     int64_t count = 0;
 };
 cudaError_t launch_wilson_warp_multi(const MultiWalk &mw, cudaStream_t s);
+
+// Batched multi-graph traversal / TTF: per-graph views and sub-wave buffers,
+// one entry (graph, tree of its sub-wave) per warp (or per grid row).
+struct MultiSub {
+    const GraphView *graphs = nullptr;
+    const WaveView *waves = nullptr;
+    const int2 *entry = nullptr;
+    int64_t count = 0;
+};
+
+// The tree a warp / grid row works on: table row `row` of a batched launch,
+// or tree `row` of the single graph and wave passed by value.
+template <bool kMulti>
+__device__ __forceinline__ bool pick_tree(const MultiSub &ms, const GraphView &g_in,
+                                          const WaveView &w_in, int64_t row, GraphView &g,
+                                          WaveView &w, int64_t &t) {
+    if constexpr (kMulti) {
+        if (row >= ms.count) return false;
+        const int2 e = ms.entry[row];
+        g = ms.graphs[e.x];
+        w = ms.waves[e.x];
+        t = e.y;
+        return true;
+    } else {
+        g = g_in;
+        w = w_in;
+        t = row;
+        return t < w.B;
+    }
+}
+// multi-graph chunked traversal (sizes, volumes, offsets, then DFN; preorder for
+// waves with a BIT array) and TTF over tables built by the host; the caller
+// zeroes each sub-wave's size and vol (and bit, f) first.  max_n: largest n.
+cudaError_t launch_traverse_multi(const MultiSub &ms, cudaStream_t s);
+cudaError_t launch_ttf_scan_multi(const MultiSub &ms, int64_t max_n, cudaStream_t s);
+cudaError_t launch_ttf_bit_multi(const MultiSub &ms, cudaStream_t s);
 cudaError_t launch_wilson(const GraphView &g, WaveView w, uint64_t seed, const int64_t *sids,
                           int64_t step_cap, cudaStream_t s, const int32_t *sorder = nullptr,
                           int32_t *rs_q = nullptr, int32_t *rs_pos = nullptr,

@@ -110,6 +110,7 @@ _SIGS = {
     "kc_graph_release_workspace": (ctypes.c_int, [_P]),
     "kc_graph_reset": (ctypes.c_int, [_P, ctypes.c_uint64, ctypes.c_int64]),
     "kc_sample": (ctypes.c_int, [_P, ctypes.c_uint64, ctypes.c_int64]),
+    "kc_reserve": (ctypes.c_int, [_P, ctypes.c_int64]),
     "kc_sample_multi": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.POINTER(ctypes.c_uint64),
                                        ctypes.POINTER(ctypes.c_int64), ctypes.c_int32]),
     "kc_estimate": (ctypes.c_int, [_P, ctypes.c_double, ctypes.c_double,
@@ -332,6 +333,9 @@ class KemenyGraph:
 
     def sample(self, seed: int, n_trees: int):
         kc_sample(self.h, seed, n_trees)
+
+    def reserve(self, n_trees: int):
+        _check(load().kc_reserve(self.h, n_trees), "kc_reserve", self.h)
 
     def estimate(self, eps: float = 0.0, delta: float = 0.05) -> float:
         return kc_estimate(self.h, eps, delta)

@@ -124,6 +124,7 @@ def test_launch_shape_does_not_change_trees():
     with kc.KemenyGraph.from_graph(g) as A, \
             kc.KemenyGraph.from_graph(g, _cfg(max_trees_in_flight=1)) as B, \
             kc.KemenyGraph.from_graph(g, _cfg(walker=kc.KC_WALK_LANE, max_trees_in_flight=7)) as C:
+        A.reserve(64)  # capacity reserved ahead changes nothing in the results
         A.sample(9, 64)
         for _ in range(4):
             B.sample(9, 16)
