@@ -1,14 +1,18 @@
 // Wilson's loop-erased-walk sampler (Sec. 2.2; Algorithm 1, "wilson(G, r)").
 //
-// One lane owns one tree.  The lane runs Wilson's algorithm as a flat state
-// machine (SEEK a start vertex outside the tree, WALK, count the loop-erased
-// path, commit it) so that every loop iteration issues at most one dependent
-// gather and the warp re-converges every iteration.  The departure of u on its
-// k-th visit follows neighbour bounded(seed, u, k, sample, WALK, deg u): loop
-// erasure is implicit (next[u] is overwritten on the next departure) and the
-// resulting tree and step count do not depend on the start order.
+// Two walkers.  k_wilson_warp (the default) runs 32 concurrent walkers of one
+// tree per warp (described below).  k_wilson runs one tree per lane as a flat
+// state machine (SEEK a start vertex outside the tree, WALK, count the
+// loop-erased path, commit it); every iteration does its phase's arithmetic,
+// then one gather, then the phase's resolution, so lanes in different phases
+// share one memory round trip.  Both can be chained (the lane walker stops at a
+// start boundary and the warp walker resumes the tree).  The departure of u on
+// its k-th visit follows neighbour bounded(seed, u, k, sample, WALK, deg u): in
+// the lane walker loop erasure is implicit (next[u] is overwritten on the next
+// departure), and by cycle popping the tree and step count depend neither on
+// the start order nor on the walker.
 //
-// Per step the lane touches one 32-byte vertex record (degree, offset and the
+// Per step a walker touches one 32-byte vertex record (degree, offset and the
 // first neighbours) and the 8-byte walker word of the next vertex; both loads
 // are issued together.  Committing a path of length L writes the words with
 // the in-tree flag and depth and the path, parent first, into `ord`.
@@ -181,7 +185,8 @@ __global__ void __launch_bounds__(128) k_wilson(GraphView g, WaveView w, uint64_
 //     parent-first order).
 // Everything is warp-synchronous: one memory action per lane per iteration,
 // claims resolved with __match_any_sync (lowest lane wins), wait cycles found
-// by pointer chasing over shuffles.  No lane ever spins on another warp.
+// every 4th iteration by pointer doubling over shuffles.  No lane ever spins on
+// another warp.
 //
 // Word of a vertex outside the tree: bits 0..31 next, 32..56 departures,
 // 57..61 owner lane, 62 owned; in-tree words are as in the lane variant.
