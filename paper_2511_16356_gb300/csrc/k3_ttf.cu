@@ -8,9 +8,10 @@
 // (Theorem 4 with the d(u) weight of Algorithm 1 and the reverse undo written as
 // the negation of its add).  Two kernels evaluate it:
 //
-//  SCAN: for each v, walk up tau0 (at most ecc(r) steps) and test tau-ancestry
-//        with the DFN intervals of tau: O(n ecc) work, all vertices of all trees
-//        in parallel.  Used when ecc(r) is small (the O(n Delta) bound of Thm 8).
+//  SCAN: for each v, walk up tau0 (at most its depth: ecc(r) for the BFS tree)
+//        and test tau-ancestry with the DFN intervals of tau: O(n ecc) work, all
+//        vertices of all trees in parallel.  Used when the depth is small (the
+//        O(n Delta) bound of Thm 8).
 //  BIT:  Algorithm 1: a DFS over tau in preorder keeps, for the tau-ancestors of
 //        the current vertex, range adds over tau0-DFN intervals in a Fenwick
 //        array and queries the point in0(v).  O(n log n) per tree.  A warp owns a
@@ -18,6 +19,8 @@
 //        are loaded first, then the 32 visits are replayed in lane order with the
 //        stack held in registers, each range add both issued to the Fenwick array
 //        (integer atomics) and folded into the pending queries of later lanes.
+// Both are templates: the batched instances take (graph, tree) entries and
+// per-graph tables, so trees of many graphs share one launch.
 #include <algorithm>
 
 #include "kc_common.cuh"

@@ -1,5 +1,6 @@
 // Host side of the C ABI declared in include/kc.h: handle lifetime, graph
-// setup, wave planning for kc_sample, the stopping rule of kc_estimate, pool
+// setup, wave planning for kc_sample (pipelined waves, batched multi-graph
+// waves), the stopping rule of kc_estimate, sample maintenance, pool
 // bookkeeping and the test hooks.  All arithmetic of the method runs in the
 // kernels of the other translation units; this file only moves data, sizes
 // launches and reads back scalars.
