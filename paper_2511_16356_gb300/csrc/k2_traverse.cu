@@ -20,6 +20,8 @@
 // replaced by one leaf-to-root pass of atomic reports (below).
 #include <algorithm>
 
+#include <cuda/atomic>
+
 #include "kc_common.cuh"
 
 namespace kc {
@@ -80,19 +82,20 @@ __global__ void __launch_bounds__(128) k_bottom_up(GraphView g, WaveView w) {
 
 // Where any valid DFN will do, subtree sizes, volumes and sibling offsets come
 // from one fully parallel pass instead of the chunked (a) + (b): every leaf
-// starts a thread that reports its totals to its parent with atomic adds and
-// decrements the parent's count of unreported children; the thread that
-// reports last continues with the parent's totals.  A child's offset is the
-// value its atomic add to the parent's size returns (siblings are ordered as
-// they report; the order may differ between runs, the DFN stays valid and f,
-// sizes and volumes do not change).  The count of unreported children lives in
-// the high half of the walker word, whose departure count / depth is no longer
-// needed once the tree is complete.  din marks leaves before the pass (-1; -2
-// for a vertex with children) and holds the offsets after it, so a vertex whose
-// count drops to zero during the pass is never mistaken for a leaf.
-__device__ __forceinline__ uint32_t *pending_of(uint64_t *word, int64_t v) {
-    return reinterpret_cast<uint32_t *>(word + v) + 1;
-}
+// starts a thread that reports its totals to its parent, and the thread that
+// reports last continues with the parent's totals.  During the pass the walker
+// word of a vertex is its report accumulator -- count of unreported children in
+// the high half, sum of the reported children's sizes in the low half -- so one
+// 64-bit atomic add (size in, one child out) tells a child both its offset
+// among its siblings (the old size sum) and whether it reported last, and the
+// last child has the parent's size without another read.  Volumes go to the
+// parent with a relaxed add before that release add; the last child reads the
+// parent's volume after an acquire fence.  Siblings are ordered as they
+// report (the order may differ between runs; the DFN stays valid and f, sizes
+// and volumes do not change).  The parent moves to din for the pass; a vertex
+// writes its parent back into its word (as an in-tree word) when it reports,
+// then its offset into din.  A vertex with children never has a zero word, so
+// only leaves start threads.
 __device__ __forceinline__ int32_t parent_of(const uint64_t *word, int64_t v) {
     return *reinterpret_cast<const int32_t *>(word + v);  // low half only
 }
@@ -101,15 +104,13 @@ __global__ void k_tree_prep(GraphView g, WaveView w) {
     const int64_t n = g.n;
     const int64_t t = blockIdx.y;
     uint64_t *word = w.word + wave_tree(w, t) * n;
-    int32_t *size = w.size + t * n;
     int64_t *vol = w.vol + t * n;
     int32_t *din = w.din + t * n;
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
          v += (int64_t)gridDim.x * blockDim.x) {
-        *pending_of(word, v) = 0u;
-        size[v] = 0;
+        din[v] = parent_of(word, v);
+        word[v] = 0ull;
         vol[v] = 0;
-        din[v] = -1;
     }
 }
 
@@ -117,14 +118,11 @@ __global__ void k_child_count(GraphView g, WaveView w) {
     const int64_t n = g.n;
     const int64_t t = blockIdx.y;
     uint64_t *word = w.word + wave_tree(w, t) * n;
-    int32_t *din = w.din + t * n;
+    const int32_t *din = w.din + t * n;
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
          v += (int64_t)gridDim.x * blockDim.x) {
-        const int32_t par = parent_of(word, v);
-        if (par >= 0 && par < n) {
-            atomicAdd(pending_of(word, par), 1u);
-            din[par] = -2;
-        }
+        const int32_t par = din[v];
+        if (par >= 0 && par < n) atomicAdd((unsigned long long *)(word + par), 1ull << 32);
     }
 }
 
@@ -137,30 +135,35 @@ __global__ void k_leaf_up(GraphView g, WaveView w) {
     int32_t *din = w.din + t * n;
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
          v += (int64_t)gridDim.x * blockDim.x) {
-        if (din[v] != -1) continue;  // has children: finished by its last child's thread
+        if (*(volatile unsigned long long *)(word + v) != 0ull) continue;  // has children
         int32_t x = (int32_t)v;
         int32_t sx = 1;
         int64_t vx = (int64_t)g.deg[v];
-        int64_t hop = 0;
-        for (;; ++hop) {
+        for (int64_t hop = 0;; ++hop) {
             if (hop > n) {  // longer than any root path: corrupt parent array
                 atomicOr(w.err, kErrBadTree);
                 break;
             }
+            const int32_t p = din[x];
             size[x] = sx;
             vol[x] = vx;
-            const int32_t p = parent_of(word, x);
             if (p < 0 || p >= n) {
+                word[x] = w_make(-1, 0, true);
                 din[x] = 0;
                 if (p >= n) atomicOr(w.err, kErrBadTree);
                 break;
             }
-            din[x] = atomicAdd(size + p, sx);
             atomicAdd((unsigned long long *)(vol + p), (unsigned long long)vx);
-            __threadfence();
-            if (atomicSub(pending_of(word, p), 1u) != 1u) break;
-            __threadfence();
-            sx = 1 + *(volatile int32_t *)(size + p);
+            cuda::atomic_ref<unsigned long long, cuda::thread_scope_device> acc(
+                *reinterpret_cast<unsigned long long *>(word + p));
+            const unsigned long long old =
+                acc.fetch_add((unsigned long long)(uint32_t)sx - (1ull << 32),
+                              cuda::memory_order_release);
+            word[x] = w_make(p, 0, true);
+            din[x] = (int32_t)(uint32_t)old;
+            if ((old >> 32) != 1ull) break;  // siblings still to report
+            cuda::atomic_thread_fence(cuda::memory_order_acquire, cuda::thread_scope_device);
+            sx = 1 + (int32_t)(uint32_t)old + sx;
             vx = (int64_t)g.deg[p] + *(volatile long long *)(vol + p);
             x = p;
         }
