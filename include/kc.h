@@ -120,7 +120,13 @@ typedef struct {
     int32_t inputs_on_device;   /* 1: kc_graph_create arrays are device pointers      */
     int32_t r_source;           /* KC_R_*                                            */
     int32_t walker;             /* KC_WALK_*: walkers per tree                        */
-    int32_t reserved0;
+    int32_t autotune;           /* 1: the first kc_sample call with at least 64 trees
+                                   times two pilot waves -- 32 walkers per tree with
+                                   the chunked traversal, then one walker per tree
+                                   with the leaf-to-root traversal (SCAN graphs) --
+                                   and keeps the faster walker and traversal; the
+                                   pilots' trees join the pool (every variant gives
+                                   the same trees).  Overrides `walker`.            */
     int64_t max_trees_in_flight; /* 0: chosen from free device memory               */
     int64_t batch_trees;        /* kc_estimate batch size (0: 1024)                 */
     int64_t max_trees;          /* kc_estimate cap on the pool size (0: 1 << 24)     */
@@ -292,6 +298,11 @@ typedef struct {
     double wf_sum, w_sum, x2_sum; /* sum w f/(2m), sum w, sum (f/2m)^2 over the pool */
     double last_resistance;      /* R(u,v) used by the last insertion            */
     int64_t last_cg_iters;       /* CG iterations of the last computed R          */
+    int32_t traversal;           /* traversal for f: 1 chunked, 2 leaf-to-root      */
+    int32_t tuned;               /* 1 once the autotuner has chosen                 */
+    double tune_ms[4];           /* autotuner pilots: walk ms per tree (32 walkers,
+                                   1 walker), traversal ms per tree (chunked,
+                                   leaf-to-root); 0 when not measured              */
 } kc_stats_t;
 
 kc_status kc_stats(kc_graph *g, kc_stats_t *out);

@@ -287,6 +287,7 @@ int64_t step_cap_of(const kc_graph *g) {
 // Traversal for f only: leaf-to-root atomics on large graphs with shallow trees
 // (low eccentricity), the chunked warp-per-tree pass otherwise.
 int fast_traversal(const kc_graph *g) {
+    if (g->trav_mode >= 0) return g->trav_mode;
     return (g->ttf_variant == KC_TTF_SCAN && g->n >= (1 << 16)) ? kTravLeafUp : kTravChunked;
 }
 
@@ -471,7 +472,8 @@ void run_wave_pipelined(kc_graph *g, Plan &p, int64_t B, int64_t sid0) {
 void run_wave(kc_graph *g, Plan &p, int64_t B, int64_t sid0, bool canonical = false) {
     // pipelining pays when traversal and TTF take long enough to hide: several
     // sub-waves, or large graphs; short waves of small graphs run straight
-    if (!canonical && g->walker == KC_WALK_WARP && B > 1 && (B > p.BT || g->n >= (1 << 16))) {
+    if (!canonical && !g->tuning && g->walker == KC_WALK_WARP && B > 1 &&
+        (B > p.BT || g->n >= (1 << 16))) {
         try {
             run_wave_pipelined(g, p, B, sid0);
         } catch (Fail &) {
@@ -1100,6 +1102,59 @@ PoolSums reduce_pool(kc_graph *g) {
     return s;
 }
 
+// One wave of B trees appended to the pool.
+void sample_wave(kc_graph *g, Plan &p, int64_t B, int64_t sid0) {
+    run_wave(g, p, B, sid0);
+    Carved c = carve(g, p);
+    WaveView w = c.wv;
+    w.B = B;
+    {
+        Phase ph(g, g->t_reduce);
+        KC_CK(g, launch_pool_append(w, g->pool, g->d_f, g->d_w, g->d_steps, g->d_sid, c.sids,
+                                    g->cfg.keep_trees ? g->d_parents : nullptr, g->n,
+                                    g->stream));
+        ph.done(g->cfg.keep_trees ? 2 : 1);
+    }
+    for (int64_t k = 0; k < B; ++k) g->h_modified[(size_t)(g->pool + k)] = 0;
+    g->pool += B;
+    g->last_wave = B;
+}
+
+// The autotuner's two pilot waves of B trees each (32 walkers per tree with the
+// chunked traversal, then one walker per tree with the leaf-to-root traversal
+// where the TTF is the tau0 scan), timed phase by phase without pipelining;
+// the faster walker and traversal are kept.  The trees are the same either way.
+void autotune(kc_graph *g, Plan &p, int64_t B, int64_t sid0) {
+    g->tuning = true;
+    const bool scan = g->ttf_variant == KC_TTF_SCAN;
+    const int modes[2] = {kTravChunked, scan ? kTravLeafUp : kTravChunked};
+    const int walkers[2] = {KC_WALK_WARP, KC_WALK_LANE};
+    double wms[2], tms[2];
+    try {
+        for (int k = 0; k < 2; ++k) {
+            g->walker = walkers[k];
+            g->trav_mode = modes[k];
+            const double w0 = g->t_wilson.ms, t0 = g->t_traverse.ms;
+            sample_wave(g, p, B, sid0 + k * B);
+            wms[k] = (g->t_wilson.ms - w0) / (double)B;
+            tms[k] = (g->t_traverse.ms - t0) / (double)B;
+        }
+    } catch (Fail &) {
+        g->tuning = false;
+        g->walker = KC_WALK_WARP;
+        g->trav_mode = -1;
+        throw;
+    }
+    g->tuning = false;
+    g->walker = wms[1] < wms[0] ? KC_WALK_LANE : KC_WALK_WARP;
+    g->trav_mode = (scan && tms[1] < tms[0]) ? kTravLeafUp : kTravChunked;
+    g->tune_ms[0] = wms[0];
+    g->tune_ms[1] = wms[1];
+    g->tune_ms[2] = tms[0];
+    g->tune_ms[3] = scan ? tms[1] : 0.0;
+    g->tuned = true;
+}
+
 void do_sample(kc_graph *g, int64_t ntrees) {
     if (ntrees <= 0) return;
     ensure_pool(g, g->pool + ntrees);
@@ -1107,27 +1162,26 @@ void do_sample(kc_graph *g, int64_t ntrees) {
     ensure_ws(g, p);
     const int64_t pool0 = g->pool, sid_base = g->next_sid;
     int64_t done = 0;
+    if (g->cfg.autotune && !g->tuned && ntrees >= 64) {
+        const int64_t B = std::min<int64_t>(p.BW, ntrees / 2);
+        try {
+            autotune(g, p, B, sid_base);
+        } catch (Fail &) {
+            g->pool = pool0;
+            g->next_sid = sid_base;
+            throw;
+        }
+        done = 2 * B;
+    }
     try {
         // equal waves: a short last wave would take as long as a full one
-        const int64_t waves = (ntrees + p.BW - 1) / p.BW;
-        const int64_t per_wave = (ntrees + waves - 1) / waves;
+        const int64_t rest = ntrees - done;
+        const int64_t waves = (rest + p.BW - 1) / p.BW;
+        const int64_t per_wave = waves > 0 ? (rest + waves - 1) / waves : 0;
         while (done < ntrees) {
             const int64_t B = std::min<int64_t>(per_wave, ntrees - done);
-            run_wave(g, p, B, sid_base + done);
-            Carved c = carve(g, p);
-            WaveView w = c.wv;
-            w.B = B;
-            {
-                Phase ph(g, g->t_reduce);
-                KC_CK(g, launch_pool_append(w, g->pool, g->d_f, g->d_w, g->d_steps, g->d_sid,
-                                            c.sids, g->cfg.keep_trees ? g->d_parents : nullptr,
-                                            g->n, g->stream));
-                ph.done(g->cfg.keep_trees ? 2 : 1);
-            }
-            for (int64_t k = 0; k < B; ++k) g->h_modified[(size_t)(g->pool + k)] = 0;
-            g->pool += B;
+            sample_wave(g, p, B, sid_base + done);
             done += B;
-            g->last_wave = B;
         }
     } catch (Fail &) {
         g->pool = pool0;
@@ -1589,7 +1643,7 @@ kc_status kc_graph_create(int64_t n, const int64_t *row_off, const int32_t *col,
         // long trees of road-shaped graphs about 4 steps per iteration, so they
         // are the default on every graph.
         int walker = cfg.walker;
-        if (walker == KC_WALK_AUTO) walker = KC_WALK_WARP;
+        if (walker == KC_WALK_AUTO || cfg.autotune) walker = KC_WALK_WARP;
         g->walker = walker;
     } catch (Fail &f) {
         kc_graph_destroy(g);
@@ -1899,6 +1953,9 @@ kc_status kc_stats(kc_graph *g, kc_stats_t *out) {
     out->trees_resampled = g->trees_resampled;
     out->last_resistance = g->last_r;
     out->last_cg_iters = g->last_cg_iters;
+    out->traversal = fast_traversal(g) == kTravLeafUp ? 2 : 1;
+    out->tuned = g->tuned ? 1 : 0;
+    for (int k = 0; k < 4; ++k) out->tune_ms[k] = g->tune_ms[k];
     out->ms_wilson = g->t_wilson.ms;
     out->ms_traverse = g->t_traverse.ms;
     out->ms_ttf = g->t_ttf.ms;

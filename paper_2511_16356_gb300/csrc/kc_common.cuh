@@ -210,6 +210,10 @@ struct kc_graph {
     int64_t pool = 0, pool_cap = 0;
     int64_t next_sid = 0;
     int64_t ws_limit = 0;  // workspace byte budget (0: a share of free memory)
+    int trav_mode = -1;     // kTrav* for f, -1: chosen from the graph
+    bool tuning = false;    // pilot waves of the autotuner (no pipelining)
+    bool tuned = false;
+    double tune_ms[4] = {0, 0, 0, 0};
     int64_t *d_f = nullptr;
     double *d_w = nullptr;
     int64_t *d_steps = nullptr;

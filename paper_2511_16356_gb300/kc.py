@@ -38,7 +38,7 @@ class kc_config(ctypes.Structure):
         ("ttf_variant", ctypes.c_int32), ("keep_trees", ctypes.c_int32),
         ("stop_rule", ctypes.c_int32), ("refresh_after_update", ctypes.c_int32),
         ("inputs_on_device", ctypes.c_int32), ("r_source", ctypes.c_int32),
-        ("walker", ctypes.c_int32), ("reserved0", ctypes.c_int32),
+        ("walker", ctypes.c_int32), ("autotune", ctypes.c_int32),
         ("max_trees_in_flight", ctypes.c_int64), ("batch_trees", ctypes.c_int64),
         ("max_trees", ctypes.c_int64), ("step_cap", ctypes.c_int64),
         ("mem_fraction", ctypes.c_double), ("sample_id_base", ctypes.c_int64),
@@ -71,6 +71,8 @@ _STATS_FIELDS = [
     ("f_sum_hi", ctypes.c_int64), ("f_sum_lo", ctypes.c_uint64),
     ("wf_sum", ctypes.c_double), ("w_sum", ctypes.c_double), ("x2_sum", ctypes.c_double),
     ("last_resistance", ctypes.c_double), ("last_cg_iters", ctypes.c_int64),
+    ("traversal", ctypes.c_int32), ("tuned", ctypes.c_int32),
+    ("tune_ms", ctypes.c_double * 4),
 ]
 
 
@@ -78,7 +80,9 @@ class kc_stats_t(ctypes.Structure):
     _fields_ = _STATS_FIELDS
 
     def as_dict(self) -> dict:
-        return {k: getattr(self, k) for k, _ in _STATS_FIELDS}
+        d = {k: getattr(self, k) for k, _ in _STATS_FIELDS}
+        d["tune_ms"] = list(d["tune_ms"])
+        return d
 
 
 class kc_server_config(ctypes.Structure):

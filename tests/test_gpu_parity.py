@@ -323,3 +323,23 @@ def test_sample_multi_equals_separate_calls_and_oracle():
     finally:
         for G in Gs:
             G.close()
+
+
+@pytest.mark.parametrize("name", ["er300", "grid17x13", "cl3000"])
+def test_autotuner_pilots_keep_trees_bit_exact(name):
+    """The autotuner's pilot waves (32 walkers + chunked traversal, then one
+    walker per tree + leaf-to-root traversal) are real trees of the pool: the
+    pool equals the oracle's, and a choice is recorded with its timings."""
+    g = SMALL[name]()
+    t0 = O.tau0(g)
+    with kc.KemenyGraph.from_graph(g, _cfg(autotune=1)) as G:
+        G.sample(13, 200)
+        st = G.stats()
+        assert st["tuned"] == 1
+        assert st["walker"] in (kc.KC_WALK_WARP, kc.KC_WALK_LANE)
+        assert st["tune_ms"][0] > 0 and st["tune_ms"][1] > 0 and st["tune_ms"][2] > 0
+        G.sample(13, 50)  # after tuning: the chosen variant
+        got = G.samples()
+        f_ref, st_ref = O.sample_batch(g, t0, 13, 0, 250)
+        assert np.array_equal(got["steps"], st_ref)
+        assert np.array_equal(got["f"], f_ref)
