@@ -1217,7 +1217,7 @@ void do_sample_multi(kc_graph *const *gs, const int64_t *n_trees, int32_t count)
             ensure_ws(g, plans[(size_t)i]);
         }
         for (;;) {
-            // this round: up to one wave per graph
+            // this pass: up to one wave per graph
             std::vector<GraphView> gv;
             std::vector<WaveView> wv;
             std::vector<uint64_t> seeds;
