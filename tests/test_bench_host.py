@@ -1,0 +1,51 @@
+"""Host-side pieces of bench.py that need no GPU: the algorithmic byte model,
+the serving workload generator, the reference arm (the CPU oracle timed on the
+host cores) and the shape of its JSON line."""
+import json
+import math
+import os
+import subprocess
+import sys
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+
+
+def test_algorithmic_bytes_model():
+    n, trees, steps = 1000, 10, 123456
+    assert bench.algorithmic_bytes("wilson", n, 5, trees, steps) == 32 * (2 * steps + 3 * n * trees)
+    assert bench.algorithmic_bytes("traverse", n, 5, trees, steps) == 32 * 6 * n * trees
+    lg = math.log2(n)
+    assert bench.algorithmic_bytes("ttf_bit", n, 5, trees, steps) == \
+        32 * (3 * lg + 4) * n * trees
+    assert bench.algorithmic_bytes("ttf_scan", n, 7, trees, steps) == 32 * 2 * 7 * n * trees
+    assert bench.algorithmic_bytes("other", n, 7, trees, steps) == 0.0
+
+
+def test_serving_workload_is_seeded_and_mixed():
+    a = bench.serve_workload(6, 5000)
+    b = bench.serve_workload(6, 5000)
+    assert [g.n for g in a] == [g.n for g in b]
+    assert all(np.array_equal(x.col, y.col) for x, y in zip(a, b))
+    assert all(1 <= g.n <= 5000 for g in a)
+    # ER, perturbed grid, Chung-Lu in turn: grids have maximum degree 4
+    assert max(a[1].deg) <= 4 and max(a[2].deg) > 4
+
+
+def test_reference_arm_prints_one_json_line():
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
+                          "--workload", "er2000", "--steps", "2", "--warmup", "3",
+                          "--ref-trees", "8"],
+                         capture_output=True, text=True, timeout=600, cwd=ROOT)
+    assert out.returncode == 0, out.stderr
+    lines = [ln for ln in out.stdout.splitlines() if ln.strip()]
+    d = json.loads(lines[-1])
+    assert d["impl"] == "reference" and d["metric"] == "trees/sec" and d["unit"] == "trees/s"
+    assert d["value"] > 0 and d["steps"] == 2 and d["warmup"] == 3
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
+    assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["value"] == d["value"]
+    assert d["higher_is_better"] is True
