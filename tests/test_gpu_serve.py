@@ -1,7 +1,6 @@
 """GPU tests of the query server (continuous batching over resident graphs):
 every result is the same alone and in a mix of concurrent traffic, and the
 same as the plain one-graph-per-call path."""
-import numpy as np
 import pytest
 
 from paper_2511_16356_gb300 import synth as S
