@@ -96,3 +96,57 @@ def test_server_config_defaults(lib):
     lib.kc_server_config_default(ctypes.byref(c))
     assert c.struct_size == ctypes.sizeof(kc.kc_server_config)
     assert c.workers == 4 and c.budget_bytes == 0 and c.request_bytes == 0
+
+
+def _struct_fields(header, name):
+    """Field names, in order, of `typedef struct { ... } name;` in a header."""
+    import re as _re
+
+    src = open(os.path.join(ROOT, "include", header)).read()
+    src = _re.sub(r"/\*.*?\*/", "", src, flags=_re.S)
+    end = _re.search(r"\}\s*" + name + r"\s*;", src)
+    assert end, name
+    start = src.rfind("typedef struct", 0, end.start())
+    body = src[src.index("{", start) + 1:end.start()]
+    fields = []
+    for decl in body.split(";"):
+        decl = decl.strip()
+        if not decl:
+            continue
+        for part in decl.split(","):
+            tok = part.strip().split()[-1]
+            fields.append(_re.sub(r"\[.*\]", "", tok).lstrip("*"))
+    return fields
+
+
+@pytest.mark.parametrize("header,name,pyname", [
+    ("kc.h", "kc_config", "kc_config"), ("kc.h", "kc_edge_op", "kc_edge_op"),
+    ("kc.h", "kc_stats_t", "kc_stats_t"), ("kc_serve.h", "kc_server_config", "kc_server_config"),
+    ("kc_serve.h", "kc_request_info", "kc_request_info")])
+def test_binding_structs_match_header_field_order(header, name, pyname):
+    from paper_2511_16356_gb300 import kc
+
+    assert [f for f, _ in getattr(kc, pyname)._fields_] == _struct_fields(header, name)
+
+
+def test_binding_struct_sizes_match_the_c_compiler(tmp_path):
+    """sizeof of every ABI struct as gcc lays it out equals the ctypes size."""
+    import ctypes
+    import shutil
+    import subprocess
+
+    from paper_2511_16356_gb300 import kc
+
+    if not shutil.which("gcc"):
+        pytest.skip("gcc not available")
+    names = ["kc_config", "kc_edge_op", "kc_stats_t", "kc_server_config", "kc_request_info"]
+    prog = tmp_path / "sizes.c"
+    prog.write_text('#include <stdio.h>\n#include "kc_serve.h"\nint main(void) {\n' +
+                    "".join(f'  printf("%zu\\n", sizeof({n}));\n' for n in names) +
+                    "  return 0;\n}\n")
+    exe = tmp_path / "sizes"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(prog), "-o", str(exe)],
+                   check=True)
+    got = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True,
+                                          check=True).stdout.split()]
+    assert got == [ctypes.sizeof(getattr(kc, n)) for n in names]
