@@ -1,7 +1,8 @@
 """CPU check of the 32-walker protocol's design (tests/walker_protocol_model.py):
 for any start order and any number of walkers the concurrent protocol pops
 exactly the cycles of sequential Wilson, so the tree, the step count, the
-depths and a parent-first order come out as the oracle's."""
+depths and a parent-first order come out as the oracle's (128 walkers: the
+walker count of a four-warp, CTA-level version of the protocol)."""
 import numpy as np
 import pytest
 
@@ -21,7 +22,7 @@ GRAPHS = {
 }
 
 
-@pytest.mark.parametrize("lanes", [32, 3])
+@pytest.mark.parametrize("lanes", [32, 3, 128])
 @pytest.mark.parametrize("order_kind", ["random", "level", "ascending"])
 @pytest.mark.parametrize("name", list(GRAPHS))
 def test_concurrent_walkers_reproduce_sequential_wilson(name, order_kind, lanes):
