@@ -224,3 +224,48 @@ def test_dfn_is_preorder_children_ascending():
         ch = sorted(v for v in range(n) if v != r and t.parent[v] == p)
         assert list(t.din[ch]) == sorted(t.din[ch])
     assert t.din[r] == 0 and t.dout[r] == n - 1
+
+
+def _curand_host_philox(seed, words):
+    """cuRAND's host-side Philox4_32_10 generator (no GPU needed).  Its i-th
+    block of four 32-bit outputs is Philox4x32-10 with key (seed low 32, seed
+    high 32) at counter (i // 65536, 0, i mod 65536, 0): 65536 subsequences in
+    counter word 2, each advanced in word 0 once per sweep."""
+    import ctypes
+    import ctypes.util
+
+    path = None
+    for cand in ("/usr/local/cuda/lib64/libcurand.so", ctypes.util.find_library("curand")):
+        if cand:
+            try:
+                lib = ctypes.CDLL(cand)
+                path = cand
+                break
+            except OSError:
+                continue
+    if path is None:
+        pytest.skip("libcurand not available")
+    gen = ctypes.c_void_p()
+    if lib.curandCreateGeneratorHost(ctypes.byref(gen), 161) != 0:  # PHILOX4_32_10
+        pytest.skip("cuRAND host generator unavailable")
+    try:
+        assert lib.curandSetPseudoRandomGeneratorSeed(gen, ctypes.c_ulonglong(seed)) == 0
+        out = np.zeros(words, dtype=np.uint32)
+        assert lib.curandGenerate(gen, out.ctypes.data_as(ctypes.c_void_p),
+                                  ctypes.c_size_t(words)) == 0
+    finally:
+        lib.curandDestroyGenerator(gen)
+    return out.reshape(-1, 4)
+
+
+@pytest.mark.parametrize("seed,blocks", [(0x123456789ABCDEF0, 250_000), (7, 4096),
+                                         (2 ** 63 + 12345, 4096)])
+def test_philox_matches_an_independent_implementation(seed, blocks):
+    """The oracle's Philox4x32-10 (rounds, multipliers, key schedule, word
+    order, key = seed split in two) equals NVIDIA's cuRAND generator block for
+    block: one million 32-bit words for the first seed."""
+    ref = _curand_host_philox(seed, 4 * blocks)
+    key = [seed & 0xFFFFFFFF, seed >> 32]
+    for i in range(blocks):
+        ctr = [i // 65536, 0, i % 65536, 0]
+        assert np.array_equal(O.philox4x32_10(ctr, key), ref[i]), i
