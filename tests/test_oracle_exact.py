@@ -162,3 +162,35 @@ def test_hutchinson_and_block_selected_inversion_agree_on_a_grid():
     assert k == pytest.approx(O.K_dense(g), rel=1e-10)
     mean, se, _ = O.K_hutchinson(g, 64, seed=3)
     assert abs(mean - k) <= 4 * se
+
+
+def _nx(g):
+    nx = pytest.importorskip("networkx")
+    G = nx.Graph()
+    G.add_nodes_from(range(g.n))
+    src = np.repeat(np.arange(g.n), g.deg)
+    G.add_edges_from((int(a), int(b)) for a, b in zip(src, g.col) if a < b)
+    return nx, G
+
+
+@pytest.mark.parametrize("name", ["er300", "grid8x6", "cl500", "K2,7", "rc9"])
+def test_exact_K_equals_networkx(name):
+    """Eq. 1 as the oracle evaluates it (dense normalised-Laplacian spectrum,
+    and the grounded-Laplacian form) against networkx's independent
+    kemeny_constant."""
+    g = {"er300": lambda: S.er_lcc(300, 0.02, 7), "grid8x6": lambda: S.grid(8, 6),
+         "cl500": lambda: S.chung_lu(500, 2.1, 6.0, 2),
+         "K2,7": lambda: S.complete_bipartite(2, 7),
+         "rc9": lambda: S.random_connected(9, 0.4, 5)}[name]()
+    nx, G = _nx(g)
+    k = nx.kemeny_constant(G)
+    assert O.K_dense(g) == pytest.approx(k, rel=1e-9)
+    assert O.K_grounded(g, 0) == pytest.approx(k, rel=1e-9)
+
+
+def test_resistance_and_tree_count_equal_networkx():
+    g = S.random_connected(10, 0.4, 8)
+    nx, G = _nx(g)
+    for u, v in [(0, 1), (2, 7), (3, 9)]:
+        assert O.resistance(g, u, v) == pytest.approx(nx.resistance_distance(G, u, v), rel=1e-9)
+    assert O.kirchhoff_count(g) == pytest.approx(float(nx.number_of_spanning_trees(G)), rel=1e-9)
