@@ -257,3 +257,23 @@ def test_unbiased_for_dfs_and_wilson_path_trees(name, kind):
         assert a == O.f_naive(g, t0, par, t.vol)
         fs.append(a)
     assert np.mean(fs) / (2 * g.m) == pytest.approx(O.K_dense(g), rel=1e-12)
+
+
+@pytest.mark.parametrize("gname", ["grid7x5", "er80", "cl400"])
+def test_path_trees_against_networkx(gname):
+    """BFS levels of tau0 equal networkx shortest-path lengths from the root,
+    and the DFS path tree equals networkx's depth-first tree (adjacency in
+    ascending id)."""
+    nx = pytest.importorskip("networkx")
+    g = {"grid7x5": lambda: S.grid(7, 5), "er80": lambda: S.er_lcc(80, 0.08, 2),
+         "cl400": lambda: S.chung_lu(400, 2.1, 6.0, 3)}[gname]()
+    G = nx.Graph()
+    G.add_nodes_from(range(g.n))
+    src = np.repeat(np.arange(g.n), g.deg)
+    G.add_edges_from((int(a), int(b)) for a, b in zip(src, g.col) if a < b)
+    bfs = O.tau0(g)
+    dist = nx.single_source_shortest_path_length(G, bfs.r)
+    assert all(bfs.level[v] == dist[v] for v in range(g.n))
+    dfs = O.tau0(g, kind="dfs")
+    pred = nx.dfs_predecessors(G, dfs.r)
+    assert all(dfs.p0[v] == pred[v] for v in range(g.n) if v != dfs.r)
