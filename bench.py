@@ -147,6 +147,34 @@ def oracle_baseline(g, trees: int, seed: int, threads: int = 0, first: int = 0):
     return trees / el, el, O.num_threads() if threads <= 0 else threads
 
 
+def host_cpu_model() -> str:
+    """The host CPU as /proc/cpuinfo names it (architecture as a fallback)."""
+    import platform
+
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                key = line.split(":")[0].strip().lower()
+                if key in ("model name", "cpu model", "hardware"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return platform.machine()
+
+
+def single_core_baseline(g, seed: int, budget_s: float = 5.0) -> dict:
+    """The oracle on one core: a small calibration batch, then about
+    `budget_s` seconds of trees."""
+    trees = 2
+    _, el, _ = oracle_baseline(g, trees, seed, threads=1)
+    if el < budget_s / 2:
+        more = int(min(1 << 20, max(1, trees * (budget_s - el) / max(el, 1e-3))))
+        _, el2, _ = oracle_baseline(g, more, seed, threads=1, first=trees)
+        trees, el = trees + more, el + el2
+    return {"value": trees / el, "unit": "trees/s", "cores": 1,
+            "sample": f"{trees} trees (sample ids 0..{trees - 1}), {el:.1f} s"}
+
+
 def run_reference(args):
     """--impl reference: the oracle timed on the host cores, same metric/config."""
     dist, rank, ws, _ = dist_setup()
@@ -544,7 +572,9 @@ def main():
         out["cpu_baseline"] = {"value": trees / el, "unit": "trees/s", "cores": used,
                                "kind": "oracle",
                                "sample": f"{trees} trees (sample ids 0..{trees - 1}) of "
-                                         f"{args.workload}, {el:.1f} s, OpenMP across trees"}
+                                         f"{args.workload}, {el:.1f} s, OpenMP across trees",
+                               "cpu": host_cpu_model(),
+                               "single_core": single_core_baseline(g, args.seed)}
     if rank == 0:
         print(json.dumps(out), flush=True)
     if dist is not None:

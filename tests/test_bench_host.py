@@ -49,3 +49,11 @@ def test_reference_arm_prints_one_json_line():
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["value"] == d["value"]
     assert d["higher_is_better"] is True
+
+
+def test_single_core_oracle_baseline_and_cpu_model():
+    from paper_2511_16356_gb300 import synth as S
+
+    d = bench.single_core_baseline(S.workload("er2000"), 1, budget_s=0.5)
+    assert d["cores"] == 1 and d["value"] > 0 and d["unit"] == "trees/s"
+    assert isinstance(bench.host_cpu_model(), str) and bench.host_cpu_model()
