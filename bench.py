@@ -203,7 +203,8 @@ def run_reference(args):
                    "trees_per_step": per_step},
         "cpu_baseline": {"value": value, "unit": "trees/s", "cores": cores, "kind": "oracle",
                          "sample": f"{per_step} trees (sample ids 0..{per_step - 1}) per step "
-                                   f"of {args.workload}, OpenMP across trees"},
+                                   f"of {args.workload}, OpenMP across trees",
+                         "cpu": host_cpu_model()},
         "e2e": {"value": value, "unit": "trees/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
