@@ -224,7 +224,9 @@ kc_status kc_sample_multi(kc_graph *const *graphs, const uint64_t *seeds, const 
  * until the stopping rule for relative error eps at failure probability delta
  * holds (Theorem 5; KC_STOP_CLT by default).  eps <= 0 returns the estimate of
  * the current pool without sampling.  K_out receives K_hat.
- * Errors: INVALID_ARG, NO_SAMPLES, OUT_OF_MEMORY, STEP_LIMIT, CUDA.
+ * Errors: INVALID_ARG, NO_SAMPLES (empty pool), OUT_OF_MEMORY, STEP_LIMIT, CUDA.
+ * Batches sampled before a failing batch stay in the pool; a call that added
+ * no tree leaves the handle's seed state as it was.
  */
 kc_status kc_estimate(kc_graph *g, double eps, double delta, double *K_out);
 

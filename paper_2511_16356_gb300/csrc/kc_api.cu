@@ -1757,8 +1757,12 @@ kc_status kc_sample_multi(kc_graph *const *graphs, const uint64_t *seeds, const 
 kc_status kc_estimate(kc_graph *g, double eps, double delta, double *K_out) {
     if (!g || !K_out) return KC_ERR_INVALID_ARG;
     if (eps > 0 && !(delta > 0 && delta < 1)) return KC_ERR_INVALID_ARG;
+    // an unseeded handle samples with seed 0; a call that adds no tree leaves
+    // the handle unseeded
+    const bool was_seeded = g->seeded;
+    const int64_t pool0 = g->pool;
     try {
-        if (!g->seeded) {
+        if (eps > 0 && !g->seeded) {
             g->seed = 0;
             g->seeded = true;
         }
@@ -1792,7 +1796,10 @@ kc_status kc_estimate(kc_graph *g, double eps, double delta, double *K_out) {
                 }
             }
         }
-        if (g->pool == 0) return KC_ERR_NO_SAMPLES;
+        if (g->pool == 0) {
+            g->seeded = was_seeded;
+            return KC_ERR_NO_SAMPLES;
+        }
         PoolSums s = reduce_pool(g);
         bool unit = true;
         for (int64_t k = 0; k < g->pool && unit; ++k) unit = !g->h_modified[(size_t)k];
@@ -1802,6 +1809,7 @@ kc_status kc_estimate(kc_graph *g, double eps, double delta, double *K_out) {
             *K_out = s.wf / s.w;
         }
     } catch (Fail &f) {
+        if (g->pool == pool0) g->seeded = was_seeded;
         return f.st;
     }
     return KC_OK;

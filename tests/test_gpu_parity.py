@@ -44,6 +44,11 @@ SMALL = {
     "path33": lambda: S.path(33),
     "K3,5": lambda: S.complete_bipartite(3, 5),
     "cl3000": lambda: S.chung_lu(3000, 2.1, 8.0, 5),
+    # the smallest graphs: one edge (every tree is the graph, f = 1), the
+    # triangle, the 3-vertex path rooted in its middle
+    "K2": lambda: S.complete(2),
+    "K3": lambda: S.complete(3),
+    "P3": lambda: S.path(3),
 }
 
 
@@ -196,6 +201,42 @@ def test_invalid_graphs_rejected(bad):
     st, h = kc.kc_graph_create(ro, col, check=False)
     assert kc.STATUS[st] == want
     assert not h
+
+
+def test_empty_and_degenerate_calls():
+    """Fewer than two vertices is rejected before any device work; zero trees
+    is a no-op; an estimate of an empty pool reports NO_SAMPLES and leaves the
+    handle unseeded; a single tree is the oracle's."""
+    for n in (0, 1):
+        st, h = kc.kc_graph_create(np.zeros(n + 1, np.int64), np.zeros(0, np.int32), check=False)
+        assert kc.STATUS[st] == "KC_ERR_INVALID_ARG" and not h
+    g = S.cycle(5)
+    t0 = O.tau0(g)
+    with kc.KemenyGraph.from_graph(g) as G:
+        with pytest.raises(kc.KcError) as e:
+            G.estimate()
+        assert e.value.name == "KC_ERR_NO_SAMPLES"
+        assert kc.kc_sample(G.h, 8, 0) == kc.KC_OK
+        G.reserve(0)
+        assert G.stats()["pool_trees"] == 0
+        assert kc.STATUS[kc.kc_sample(G.h, 8, -1, check=False)] == "KC_ERR_INVALID_ARG"
+        G.sample(8, 1)
+        ref = O.tree(g, t0, 8, 0)
+        got = G.samples()
+        assert got["f"].tolist() == [ref.f] and got["steps"].tolist() == [ref.steps]
+        assert G.estimate() == pytest.approx(ref.f / (2 * g.m), rel=1e-15)
+
+
+@pytest.mark.parametrize("name", ["K2", "P3"])
+def test_tree_graphs_estimate_is_exact(name):
+    """A graph that is a tree has one spanning tree, so every f equals
+    2m K and the estimate to any eps is exact: K2 = 1/2, P3 = 3/2."""
+    g = SMALL[name]()
+    want = {"K2": 0.5, "P3": 1.5}[name]
+    with kc.KemenyGraph.from_graph(g) as G:
+        k = G.estimate(0.01, 0.05)
+        assert k == want
+        assert set(G.samples()["f"].tolist()) == {int(2 * g.m * want)}
 
 
 def test_step_cap_reports_error_and_keeps_handle():

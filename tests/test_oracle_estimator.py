@@ -277,3 +277,17 @@ def test_path_trees_against_networkx(gname):
     dfs = O.tau0(g, kind="dfs")
     pred = nx.dfs_predecessors(G, dfs.r)
     assert all(dfs.p0[v] == pred[v] for v in range(g.n) if v != dfs.r)
+
+
+@pytest.mark.parametrize("name,n,want_f,want_steps", [("K2", 2, 1, 1), ("P3", 3, 6, 2)])
+def test_tree_graphs_every_sample_is_exact(name, n, want_f, want_steps):
+    """A graph that is itself a tree has one spanning tree: every sample is
+    the graph, each non-root vertex departs once straight into the tree, and
+    f = 2m K with K = sum_e vol_e (2m - vol_e) / 2m (Theorem 1 with one tree):
+    K2 gives 1 * 1 / 2 = 1/2, so f = 1; P3 gives 2 * (1 * 3) / 4 = 3/2, f = 6."""
+    g = S.complete(2) if name == "K2" else S.path(3)
+    assert g.n == n and g.m == n - 1
+    t0 = O.tau0(g)
+    f, steps = O.sample_batch(g, t0, 5, 0, 32)
+    assert f.tolist() == [want_f] * 32 and steps.tolist() == [want_steps] * 32
+    assert want_f / (2 * g.m) == pytest.approx(O.K_dense(g), rel=1e-12)
