@@ -12,3 +12,4 @@ from .core import *  # noqa: F401,F403
 from .exact import *  # noqa: F401,F403
 from .blocktri import *  # noqa: F401,F403
 from .hutchinson import *  # noqa: F401,F403
+from .estimate import *  # noqa: F401,F403

@@ -1,0 +1,105 @@
+"""The estimate K_hat and the rule that decides how many trees to draw.
+
+TEST INFRASTRUCTURE ONLY (see the package docstring).
+
+Theorem 3 makes f(tau) / 2m an unbiased sample of the Kemeny constant, so the
+estimate over w trees is their mean (Algorithm 1, last line), with the sum of
+f kept as an exact integer.  The paper fixes the number of trees only through
+Hoeffding's inequality (Theorem 5), which asks for far more trees than needed
+in practice.  The rule used by default reads Theorem 5's (eps, delta)
+guarantee through the normal approximation of the sample mean:
+
+* draw a pilot of max(64, min(batch, cap)) trees;
+* stop once w >= 64 and z s / sqrt(w) <= eps K_hat (1 - eps), where s is the
+  sample standard deviation of f / 2m and z the upper delta/2 quantile of the
+  standard normal (the factor 1 - eps keeps |K_hat - K| <= eps K when the
+  interval holds around K rather than K_hat);
+* otherwise draw max(batch, ceil((z s / tol)^2) - w) more trees, never past
+  the cap, for at most 64 rounds.
+
+Sums here are exact integers (Python ints and fractions), converted to floating
+point only for the comparison and the square root, so each decision is the
+exact one; ``margin`` reports how far the closest decision was from flipping.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+from fractions import Fraction
+from statistics import NormalDist
+
+import numpy as np
+
+__all__ = ["z_upper", "EstimateRun", "estimate_clt", "estimate_fixed"]
+
+
+def z_upper(p: float) -> float:
+    """z with P(Z > z) = p for a standard normal Z."""
+    return NormalDist().inv_cdf(1.0 - p)
+
+
+@dataclass
+class EstimateRun:
+    K: float                 # K_hat = sum f / (2m w)
+    trees: int               # w, trees drawn
+    rounds: int              # stopping tests made
+    margin: float = math.inf  # smallest relative distance of a decision from its threshold
+    sizes: list = field(default_factory=list)  # trees drawn per batch
+
+
+def estimate_fixed(f, twom: int) -> float:
+    """K_hat of a fixed set of trees: the exact integer sum, divided once."""
+    total = sum(int(x) for x in f)
+    return total / (twom * len(f))
+
+
+def estimate_clt(draw, twom: int, eps: float, delta: float, batch: int = 1024,
+                 cap: int = 1 << 24) -> EstimateRun:
+    """Run the normal-approximation stopping rule.
+
+    draw(first, count) returns the f values of sample ids first .. first+count-1
+    (any sampler keyed by sample id: the trees do not depend on the batching).
+    """
+    z = z_upper(delta / 2.0)
+    f: list[int] = []
+    sizes = []
+
+    def more(count):
+        vals = draw(len(f), count)
+        f.extend(int(x) for x in np.asarray(vals).tolist())
+        sizes.append(count)
+
+    pilot = max(64, min(batch, cap))
+    more(pilot)
+    margin = math.inf
+    rounds = 0
+    for _ in range(64):
+        rounds += 1
+        w = len(f)
+        sf = sum(f)
+        sf2 = sum(x * x for x in f)
+        mean = Fraction(sf, twom * w)
+        var = Fraction(w * sf2 - sf * sf, twom * twom * w * max(1, w - 1))
+        var = max(var, Fraction(0))
+        sd = math.sqrt(float(var))
+        tol = eps * float(mean) * (1.0 - eps)
+        lhs = z * sd / math.sqrt(w)
+        if tol > 0:
+            margin = min(margin, abs(lhs - tol) / tol)
+        if w >= 64 and lhs <= tol:
+            break
+        if w >= cap:
+            break
+        if tol > 0:
+            q = (z * sd / tol) ** 2
+            need = math.ceil(q)
+            if need - w >= batch:  # the shortfall, not the batch, sets the next draw
+                margin = min(margin, min(q - math.floor(q), math.ceil(q) - q) / max(q, 1.0))
+        else:
+            need = cap
+        count = min(max(need - w, batch), cap - w)
+        if count <= 0:
+            break
+        more(count)
+    return EstimateRun(K=estimate_fixed(f, twom), trees=len(f), rounds=rounds, margin=margin,
+                       sizes=sizes)

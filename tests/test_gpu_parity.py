@@ -180,6 +180,24 @@ def test_estimate_to_eps_covers_exact():
     assert misses <= 2
 
 
+@pytest.mark.parametrize("name,eps,batch", [("er300", 0.01, 64), ("cl3000", 0.005, 64),
+                                            ("grid17x13", 0.02, 100), ("er300", 0.01, 1024)])
+def test_stopping_rule_matches_oracle(name, eps, batch):
+    """kc_estimate on a fresh handle (seed 0) draws exactly the trees the
+    oracle's stopping rule draws, batch by batch, and returns its K_hat.  The
+    oracle decides with exact sums; the cases are chosen with every decision
+    far from its threshold (margin), so the device's FP64 sums decide alike."""
+    g = SMALL[name]()
+    t0 = O.tau0(g)
+    ref = O.estimate_clt(lambda a, c: O.sample_batch(g, t0, 0, a, c)[0], 2 * g.m, eps, 0.05,
+                         batch=batch)
+    assert ref.margin > 1e-9
+    with kc.KemenyGraph.from_graph(g, _cfg(batch_trees=batch)) as G:
+        k = G.estimate(eps, 0.05)
+        assert G.stats()["pool_trees"] == ref.trees
+    assert k == pytest.approx(ref.K, rel=1e-12)
+
+
 @pytest.mark.parametrize("bad", ["asym", "loop", "multi", "disconnected", "unsorted"])
 def test_invalid_graphs_rejected(bad):
     g = S.cycle(6)
