@@ -198,6 +198,22 @@ def test_stopping_rule_matches_oracle(name, eps, batch):
     assert k == pytest.approx(ref.K, rel=1e-12)
 
 
+@pytest.mark.parametrize("name,eps", [("K7", 0.5), ("C40", 1.0)])
+def test_hoeffding_rule_draws_theorem5_trees(name, eps):
+    """With the Hoeffding rule kc_estimate draws exactly Theorem 5's sample size
+    (Delta read as ecc(r), kappa >= (n-1)^2/n), sample ids 0.., and K_hat is the
+    oracle's mean over those trees; the sizes (1969, 13063) sit far from an
+    integer boundary."""
+    g = SMALL[name]()
+    t0 = O.tau0(g)
+    want = O.hoeffding_trees(g.n, g.m, t0.ecc, eps, 0.05)
+    with kc.KemenyGraph.from_graph(g, _cfg(stop_rule=kc.KC_STOP_HOEFFDING)) as G:
+        k = G.estimate(eps, 0.05)
+        assert G.stats()["pool_trees"] == want
+    f, _ = O.sample_batch(g, t0, 0, 0, want)
+    assert k == pytest.approx(O.estimate_fixed(f, 2 * g.m), rel=1e-12)
+
+
 @pytest.mark.parametrize("bad", ["asym", "loop", "multi", "disconnected", "unsorted"])
 def test_invalid_graphs_rejected(bad):
     g = S.cycle(6)
