@@ -147,18 +147,35 @@ def oracle_baseline(g, trees: int, seed: int, threads: int = 0, first: int = 0):
     return trees / el, el, O.num_threads() if threads <= 0 else threads
 
 
-def host_cpu_model() -> str:
-    """The host CPU as /proc/cpuinfo names it (architecture as a fallback)."""
+# Arm cores by (implementer, part) of the main ID register, as /proc/cpuinfo
+# prints them on aarch64 hosts, which give no model name
+ARM_PARTS = {("0x41", "0xd0c"): "Arm Neoverse N1", ("0x41", "0xd40"): "Arm Neoverse V1",
+             ("0x41", "0xd49"): "Arm Neoverse N2", ("0x41", "0xd4f"): "Arm Neoverse V2",
+             ("0x41", "0xd84"): "Arm Neoverse V3"}
+
+
+def host_cpu_model(cpuinfo: str = "/proc/cpuinfo") -> str:
+    """The host CPU as /proc/cpuinfo names it: the model name on x86, the core
+    type from the implementer and part numbers on Arm, else the architecture."""
     import platform
 
+    fields = {}
     try:
-        with open("/proc/cpuinfo") as f:
+        with open(cpuinfo) as f:
             for line in f:
-                key = line.split(":")[0].strip().lower()
-                if key in ("model name", "cpu model", "hardware"):
-                    return line.split(":", 1)[1].strip()
+                if ":" not in line:
+                    continue
+                key, val = (x.strip() for x in line.split(":", 1))
+                fields.setdefault(key.lower(), val)
     except OSError:
         pass
+    for key in ("model name", "cpu model", "hardware"):
+        if fields.get(key):
+            return fields[key]
+    impl, part = fields.get("cpu implementer", "").lower(), fields.get("cpu part", "").lower()
+    if impl and part:
+        name = ARM_PARTS.get((impl, part), f"implementer {impl} part {part}")
+        return f"{platform.machine()} {name}"
     return platform.machine()
 
 

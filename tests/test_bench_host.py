@@ -57,3 +57,12 @@ def test_single_core_oracle_baseline_and_cpu_model():
     d = bench.single_core_baseline(S.workload("er2000"), 1, budget_s=0.5)
     assert d["cores"] == 1 and d["value"] > 0 and d["unit"] == "trees/s"
     assert isinstance(bench.host_cpu_model(), str) and bench.host_cpu_model()
+
+
+def test_cpu_model_on_arm_hosts(tmp_path):
+    info = tmp_path / "cpuinfo"
+    info.write_text("processor\t: 0\nBogoMIPS\t: 2000.00\nCPU implementer\t: 0x41\n"
+                    "CPU architecture: 8\nCPU variant\t: 0x0\nCPU part\t: 0xd4f\n\n")
+    assert bench.host_cpu_model(str(info)).endswith("Arm Neoverse V2")
+    info.write_text("processor\t: 0\nmodel name\t: Some x86 CPU @ 2.00GHz\n")
+    assert bench.host_cpu_model(str(info)) == "Some x86 CPU @ 2.00GHz"
