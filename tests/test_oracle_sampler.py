@@ -258,6 +258,19 @@ def _curand_host_philox(seed, words):
     return out.reshape(-1, 4)
 
 
+@pytest.mark.parametrize("ctr,key,want", [
+    ([0, 0, 0, 0], [0, 0], [0x6627E8D5, 0xE169C58D, 0xBC57AC4C, 0x9B00DBD8]),
+    ([0xFFFFFFFF] * 4, [0xFFFFFFFF] * 2, [0x408F276D, 0x41C83B0E, 0xA20BC7C6, 0x6D5451FD]),
+    ([0x243F6A88, 0x85A308D3, 0x13198A2E, 0x03707344], [0xA4093822, 0x299F31D0],
+     [0xD16CFE09, 0x94FDCCEB, 0x5001E420, 0x24126EA1]),
+])
+def test_philox_known_answer_vectors(ctr, key, want):
+    """Philox4x32-10 known-answer vectors published with the generator's
+    reference implementation (Salmon et al., SC'11): zero input, all-ones input,
+    and the digits of pi as counter and key."""
+    assert O.philox4x32_10(ctr, key).tolist() == want
+
+
 @pytest.mark.parametrize("seed,blocks", [(0x123456789ABCDEF0, 250_000), (7, 4096),
                                          (2 ** 63 + 12345, 4096)])
 def test_philox_matches_an_independent_implementation(seed, blocks):
