@@ -31,7 +31,8 @@ def nvcc() -> str:
 
 def _compile(src: str, extra) -> str:
     obj = os.path.join(OBJ, os.path.basename(src) + ".o")
-    deps = glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(ROOT, "include", "*.h")) + [src]
+    deps = (glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(CSRC, "*.h")) +
+            glob.glob(os.path.join(ROOT, "include", "*.h")) + [src])
     if os.path.exists(obj) and all(os.path.getmtime(obj) >= os.path.getmtime(d) for d in deps):
         return obj
     cmd = [nvcc(), *ARCH, *FLAGS, *extra, "-c", src, "-o", obj]

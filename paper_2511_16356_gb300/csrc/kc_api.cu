@@ -17,6 +17,7 @@
 #include <vector>
 
 #include "kc_common.cuh"
+#include "kc_host_graph.h"
 
 namespace kc {
 cudaError_t launch_out_from_size(int64_t n, const int32_t *din, const int32_t *size,
@@ -738,15 +739,9 @@ void traverse_tau0(kc_graph *g, int &launches) {
     launches += 4 + nl;
 }
 
-
 // ===========================================================================
 // Sample maintenance (Algorithms 2 and 3)
 // ===========================================================================
-bool has_edge_h(const std::vector<int64_t> &ro, const std::vector<int32_t> &col, int32_t a,
-                int32_t b) {
-    return std::binary_search(col.begin() + ro[(size_t)a], col.begin() + ro[(size_t)a + 1], b);
-}
-
 // insert or erase (u, v) and (v, u) in a CSR kept sorted row by row
 void mutate_csr(std::vector<int64_t> &ro, std::vector<int32_t> &col, int32_t u, int32_t v,
                 bool insert) {
@@ -760,28 +755,11 @@ void mutate_csr(std::vector<int64_t> &ro, std::vector<int32_t> &col, int32_t u, 
     }
 }
 
-bool connected_h(const std::vector<int64_t> &ro, const std::vector<int32_t> &col) {
-    const int64_t n = (int64_t)ro.size() - 1;
-    std::vector<uint8_t> seen((size_t)n, 0);
-    std::vector<int32_t> q;
-    q.reserve((size_t)n);
-    q.push_back(0);
-    seen[0] = 1;
-    for (size_t h = 0; h < q.size(); ++h) {
-        const int32_t x = q[h];
-        for (int64_t e = ro[(size_t)x]; e < ro[(size_t)x + 1]; ++e)
-            if (!seen[(size_t)col[(size_t)e]]) {
-                seen[(size_t)col[(size_t)e]] = 1;
-                q.push_back(col[(size_t)e]);
-            }
-    }
-    return (int64_t)q.size() == n;
-}
-
-// The whole batch against the evolving graph, before anything is applied.
+// The whole batch against the evolving graph, before anything is applied.  The
+// graph is connected before the batch and every accepted op keeps it so; a
+// deletion then keeps it connected exactly when its endpoints stay connected.
 kc_status validate_batch(kc_graph *g, const kc_edge_op *ops, int64_t n_ops) {
-    std::vector<int64_t> ro = g->h_row_off;
-    std::vector<int32_t> col = g->h_col;
+    kc_host::OverlayGraph og(g->h_row_off.data(), g->h_col.data(), g->n);
     for (int64_t i = 0; i < n_ops; ++i) {
         const kc_edge_op &o = ops[i];
         if (o.u < 0 || o.v < 0 || o.u >= g->n || o.v >= g->n || o.u == o.v ||
@@ -789,11 +767,15 @@ kc_status validate_batch(kc_graph *g, const kc_edge_op *ops, int64_t n_ops) {
             return KC_ERR_INVALID_ARG;
         if (o.op == 0 && g->cfg.r_source == KC_R_GIVEN && !(o.r > 0.0 && o.r <= 1.0))
             return KC_ERR_INVALID_ARG;
-        const bool present = has_edge_h(ro, col, o.u, o.v);
+        const bool present = og.has_edge(o.u, o.v);
         if (o.op == 0 && present) return KC_ERR_EDGE_EXISTS;
         if (o.op == 1 && !present) return KC_ERR_EDGE_MISSING;
-        mutate_csr(ro, col, o.u, o.v, o.op == 0);
-        if (o.op == 1 && !connected_h(ro, col)) return KC_ERR_BRIDGE;
+        if (o.op == 0) {
+            og.insert(o.u, o.v);
+        } else {
+            og.erase(o.u, o.v);
+            if (!og.connected(o.u, o.v)) return KC_ERR_BRIDGE;
+        }
     }
     return KC_OK;
 }
