@@ -244,7 +244,9 @@ typedef struct {
  * the retained trees, their f and weights.  The whole batch is validated
  * against the evolving graph first; on any invalid op nothing is applied.
  * Requires keep_trees.  Errors: INVALID_ARG, EDGE_EXISTS, EDGE_MISSING,
- * BRIDGE, NO_SAMPLES, NOT_RETAINED, OUT_OF_MEMORY, STEP_LIMIT, CUDA.
+ * BRIDGE, NO_SAMPLES, NOT_RETAINED, OUT_OF_MEMORY, STEP_LIMIT, CUDA.  The
+ * last three arise while ops are applied: the ops before the failing one stay
+ * applied (kc_stats().updates_applied counts them).
  */
 kc_status kc_update(kc_graph *g, const kc_edge_op *ops, int64_t n_ops, int32_t mode);
 
