@@ -246,7 +246,8 @@ typedef struct {
  * Requires keep_trees.  Errors: INVALID_ARG, EDGE_EXISTS, EDGE_MISSING,
  * BRIDGE, NO_SAMPLES, NOT_RETAINED, OUT_OF_MEMORY, STEP_LIMIT, CUDA.  The
  * last three arise while ops are applied: the ops before the failing one stay
- * applied (kc_stats().updates_applied counts them).
+ * applied (kc_stats().updates_applied counts them) and the failing one may be
+ * partly applied, so the handle should then be destroyed.
  */
 kc_status kc_update(kc_graph *g, const kc_edge_op *ops, int64_t n_ops, int32_t mode);
 
