@@ -362,11 +362,13 @@ def serve_leg(args, kc):
         "identical_results": bool(np.array_equal(np.asarray(k_s), np.asarray(k_p))),
     }
 
-# DRAM bytes per Wilson departure of k_wilson_warp on road-shaped grids: an ncu
-# capture (dram__bytes) of the kernel on the 300x300 perturbed grid with 1000
-# trees in flight moved 10.27 GB for 1.133e9 departures.  The full-size launch
-# is too long to capture; its traffic is this figure times its departures.
-WILSON_WARP_GRID_DRAM_BYTES_PER_STEP = 10.27e9 / 1.1334e9
+# DRAM bytes per Wilson departure of k_wilson_warp on road-shaped grids, from an
+# ncu capture (dram__bytes) on the 300x300 perturbed grid with 1000 trees in
+# flight; the full-size launch is too long to capture, so its traffic is this
+# figure times its departures.  None while no capture of the kernel as built
+# exists (the last one, 10.27 GB for 1.133e9 departures, predates the kernel's
+# multi-graph template).
+WILSON_WARP_GRID_DRAM_BYTES_PER_STEP = None
 
 
 def main():
@@ -489,7 +491,8 @@ def main():
                    "traverse": "k_bottom_up/k_sibling_offsets/k_top_down",
                    "ttf_bit": "k_ttf_bit", "ttf_scan": "k_ttf_scan"}[dom]
     traffic = None
-    if dom == "wilson" and st["walker"] == kc.KC_WALK_WARP and args.workload.startswith("grid"):
+    if (WILSON_WARP_GRID_DRAM_BYTES_PER_STEP is not None and dom == "wilson"
+            and st["walker"] == kc.KC_WALK_WARP and args.workload.startswith("grid")):
         traffic = WILSON_WARP_GRID_DRAM_BYTES_PER_STEP * steps_total / max(1, dom_launches)
     phase_ms = {k: round(v[0], 3) for k, v in phases.items()}
     phase_ms["wave_init"] = round(st["ms_wave_init"], 3)
