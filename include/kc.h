@@ -244,10 +244,13 @@ typedef struct {
  * the retained trees, their f and weights.  The whole batch is validated
  * against the evolving graph first; on any invalid op nothing is applied.
  * Requires keep_trees.  Errors: INVALID_ARG, EDGE_EXISTS, EDGE_MISSING,
- * BRIDGE, NO_SAMPLES, NOT_RETAINED, OUT_OF_MEMORY, STEP_LIMIT, CUDA.  The
- * last three arise while ops are applied: the ops before the failing one stay
- * applied (kc_stats().updates_applied counts them) and the failing one may be
- * partly applied, so the handle should then be destroyed.
+ * BRIDGE, NO_SAMPLES, NOT_RETAINED, OVERFLOW, OUT_OF_MEMORY, STEP_LIMIT, CUDA.
+ * OVERFLOW: 4 m^2 ecc(r) would reach 2^62 (the int64 margin of f); insertions
+ * are checked before anything is applied, a deletion that rebuilds tau0 once
+ * the new ecc(r) is known.  OVERFLOW from a rebuild and the last three arise
+ * while ops are applied: the ops before the failing one stay applied
+ * (kc_stats().updates_applied counts them) and the failing one may be partly
+ * applied, so the handle should then be destroyed.
  */
 kc_status kc_update(kc_graph *g, const kc_edge_op *ops, int64_t n_ops, int32_t mode);
 

@@ -755,11 +755,20 @@ void mutate_csr(std::vector<int64_t> &ro, std::vector<int32_t> &col, int32_t u, 
     }
 }
 
+// |f| <= 4 m^2 ecc(r) (Theorem 5's proof) must stay below 2^62 for the int64 f
+bool f_may_overflow(int64_t m, int32_t ecc) {
+    const long double bound = 4.0L * (long double)m * (long double)m * (long double)ecc;
+    return bound >= 4611686018427387904.0L;
+}
+
 // The whole batch against the evolving graph, before anything is applied.  The
 // graph is connected before the batch and every accepted op keeps it so; a
 // deletion then keeps it connected exactly when its endpoints stay connected.
+// Insertions keep tau0 (and ecc) and grow m, so the overflow margin is checked
+// for each; a deletion that rebuilds tau0 is checked when the new ecc is known.
 kc_status validate_batch(kc_graph *g, const kc_edge_op *ops, int64_t n_ops) {
     kc_host::OverlayGraph og(g->h_row_off.data(), g->h_col.data(), g->n);
+    int64_t m = g->m;
     for (int64_t i = 0; i < n_ops; ++i) {
         const kc_edge_op &o = ops[i];
         if (o.u < 0 || o.v < 0 || o.u >= g->n || o.v >= g->n || o.u == o.v ||
@@ -772,9 +781,11 @@ kc_status validate_batch(kc_graph *g, const kc_edge_op *ops, int64_t n_ops) {
         if (o.op == 1 && !present) return KC_ERR_EDGE_MISSING;
         if (o.op == 0) {
             og.insert(o.u, o.v);
+            if (f_may_overflow(++m, g->ecc)) return KC_ERR_OVERFLOW;
         } else {
             og.erase(o.u, o.v);
             if (!og.connected(o.u, o.v)) return KC_ERR_BRIDGE;
+            --m;
         }
     }
     return KC_OK;
@@ -1043,6 +1054,12 @@ void apply_delete(kc_graph *g, int32_t u, int32_t v, int32_t mode) {
     if (tau0_hit) {
         int nl = 0;
         build_tau0(g, nl);
+        g->t_update.launches += nl;
+        if (f_may_overflow(g->m, g->ecc)) {
+            g->last_error = "the rebuilt tau0 is too deep: 4 m^2 ecc(r) >= 2^62";
+            throw Fail{KC_ERR_OVERFLOW};
+        }
+        nl = 0;
         traverse_tau0(g, nl);
         g->t_update.launches += nl;
     }
@@ -1605,11 +1622,7 @@ kc_status kc_graph_create(int64_t n, const int64_t *row_off, const int32_t *col,
         build_tau0(g, launches);
         gv.ecc = g->ecc;
 
-        // overflow margin: |f| <= 4 m^2 ecc (Theorem 5's proof) must stay below 2^62
-        {
-            const long double bound = 4.0L * (long double)g->m * (long double)g->m * (long double)g->ecc;
-            if (bound >= 4611686018427387904.0L) throw Fail{KC_ERR_OVERFLOW};
-        }
+        if (f_may_overflow(g->m, g->ecc)) throw Fail{KC_ERR_OVERFLOW};
         traverse_tau0(g, launches);
         ph.done(launches);
         // TTF variant (Theorem 8: O(n min(Delta, log n)))
