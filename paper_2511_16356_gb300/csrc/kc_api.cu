@@ -991,6 +991,8 @@ double weight_sum(kc_graph *g, const std::vector<uint8_t> &flags, int which) {
 void apply_insert(kc_graph *g, int32_t u, int32_t v, int32_t mode, double r_given) {
     mutate_csr(g->h_row_off, g->h_col, u, v, true);
     upload_graph(g);
+    // the BIT kernel holds 2m in 32 bits; the scan gives the same f on any graph
+    if (g->ttf_variant == KC_TTF_BIT && 2 * g->m >= ((int64_t)1 << 31)) g->ttf_variant = KC_TTF_SCAN;
     double R = r_given;
     if (g->cfg.r_source != KC_R_GIVEN) {
         int nl = 0;
