@@ -135,16 +135,28 @@ def barrier(dist):
         dist.barrier()
 
 
+def host_cores() -> int:
+    """Host cores this process may run on (launchers such as torchrun set
+    OMP_NUM_THREADS=1, which would otherwise confine the oracle to one core)."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except (AttributeError, OSError):
+        return os.cpu_count() or 1
+
+
 def oracle_baseline(g, trees: int, seed: int, threads: int = 0, first: int = 0):
     """The CPU oracle as it stands: Wilson + traversal + Algorithm 1 over a
-    bounded sample of sample ids, OpenMP across trees on the host cores."""
+    bounded sample of sample ids, OpenMP across trees on all host cores
+    (threads = 0) or on `threads` of them."""
     import oracle as O
 
+    if threads <= 0:
+        threads = host_cores()
     t0 = O.tau0(g)
     t = time.perf_counter()
     f, steps = O.sample_batch(g, t0, seed, first, trees, threads=threads)
     el = time.perf_counter() - t
-    return trees / el, el, O.num_threads() if threads <= 0 else threads
+    return trees / el, el, threads
 
 
 # Arm cores by (implementer, part) of the main ID register, as /proc/cpuinfo

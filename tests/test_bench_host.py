@@ -66,3 +66,24 @@ def test_cpu_model_on_arm_hosts(tmp_path):
     assert bench.host_cpu_model(str(info)).endswith("Arm Neoverse V2")
     info.write_text("processor\t: 0\nmodel name\t: Some x86 CPU @ 2.00GHz\n")
     assert bench.host_cpu_model(str(info)) == "Some x86 CPU @ 2.00GHz"
+
+
+def test_reference_arm_under_torchrun_two_ranks():
+    """The multi-rank launch of the reference arm: rank 0 alone prints one
+    line (the other rank exits without work), and the oracle runs on every
+    host core although the launcher sets OMP_NUM_THREADS=1."""
+    import random
+
+    port = str(random.randint(20000, 40000))
+    out = subprocess.run([sys.executable, "-m", "torch.distributed.run", "--nnodes=1",
+                          "--nproc-per-node", "2", "--master-addr", "127.0.0.1",
+                          "--master-port", port, os.path.join(ROOT, "bench.py"),
+                          "--impl", "reference", "--gpus", "2", "--steps", "1", "--warmup", "3",
+                          "--ref-trees", "8", "--workload", "er2000"],
+                         capture_output=True, text=True, timeout=600, cwd=ROOT)
+    assert out.returncode == 0, out.stderr[-2000:]
+    lines = [ln for ln in out.stdout.splitlines() if ln.strip().startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["n_gpus"] == 2 and d["value"] > 0
+    assert d["cpu_baseline"]["cores"] == bench.host_cores()
