@@ -546,7 +546,11 @@ def main():
         cfg2.walker = cfg.walker
         cfg2.hybrid_prefix_permille = cfg.hybrid_prefix_permille
         cfg2.hybrid_tail_permille = cfg.hybrid_tail_permille
-        cfg2.batch_trees = 1024
+        # batches of one resident wave where trees are long (deep tau0: a wave
+        # lasts about as long as its slowest tree, so a wave of 1024 costs
+        # about what a full one does), 1024 trees where waves are throughput-bound
+        deep = st["ttf_variant"] == kc.KC_TTF_BIT and st["walker"] == kc.KC_WALK_WARP
+        cfg2.batch_trees = max(1024, st["resident_trees"]) if deep else 1024
         H = kc.KemenyGraph.from_graph(g, cfg2, stream=stream.cuda_stream)
         torch.cuda.synchronize()
         t = time.perf_counter()
@@ -554,6 +558,7 @@ def main():
         tte = time.perf_counter() - t
         out["time_to_eps"] = {"value": tte, "unit": "s", "eps": args.eps, "delta": args.delta,
                               "trees": H.stats()["pool_trees"], "K": k_hat,
+                              "batch_trees": int(cfg2.batch_trees),
                               "rule": "CLT: z s/sqrt(w) <= eps K (1-eps)"}
         H.close()
 

@@ -311,6 +311,11 @@ typedef struct {
     double tune_ms[4];           /* autotuner pilots: walk ms per tree (32 walkers,
                                    1 walker), traversal ms per tree (chunked,
                                    leaf-to-root); 0 when not measured              */
+    int64_t resident_trees;      /* trees the 32-walker kernel runs at once on this
+                                   GPU (SMs x resident one-warp blocks).  A wave of
+                                   up to this many trees lasts about as long as its
+                                   slowest tree, so it is the natural kc_estimate
+                                   batch where single trees are slow            */
 } kc_stats_t;
 
 kc_status kc_stats(kc_graph *g, kc_stats_t *out);

@@ -529,6 +529,16 @@ cudaError_t launch_wilson_warp(const GraphView &g, WaveView w, uint64_t seed, co
     return cudaGetLastError();
 }
 
+int wilson_warp_blocks_per_sm() {
+    int b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_wilson_warp<false>, kWarpWalkerBlock,
+                                                      0) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return 0;
+    }
+    return b;
+}
+
 cudaError_t launch_wilson_warp_multi(const MultiWalk &mw, cudaStream_t s) {
     if (mw.count <= 0) return cudaSuccess;
     k_wilson_warp<true><<<(unsigned)mw.count, kWarpWalkerBlock, 0, s>>>(

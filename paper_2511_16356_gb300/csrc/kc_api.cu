@@ -1525,6 +1525,7 @@ kc_status kc_graph_create(int64_t n, const int64_t *row_off, const int32_t *col,
             g->last_error = "the library is built for sm_103a only";
             throw Fail{KC_ERR_NO_DEVICE};
         }
+        g->resident_trees = (int64_t)prop.multiProcessorCount * wilson_warp_blocks_per_sm();
         KC_CK(g, cudaEventCreate(&g->ev0));
         KC_CK(g, cudaEventCreate(&g->ev1));
         g->n = n;
@@ -1961,6 +1962,7 @@ kc_status kc_stats(kc_graph *g, kc_stats_t *out) {
     out->traversal = fast_traversal(g) == kTravLeafUp ? 2 : 1;
     out->tuned = g->tuned ? 1 : 0;
     for (int k = 0; k < 4; ++k) out->tune_ms[k] = g->tune_ms[k];
+    out->resident_trees = g->resident_trees;
     out->ms_wilson = g->t_wilson.ms;
     out->ms_traverse = g->t_traverse.ms;
     out->ms_ttf = g->t_ttf.ms;

@@ -214,6 +214,7 @@ struct kc_graph {
     bool tuning = false;    // pilot waves of the autotuner (no pipelining)
     bool tuned = false;
     double tune_ms[4] = {0, 0, 0, 0};
+    int64_t resident_trees = 0;  // trees the 32-walker kernel runs at once on the device
     int64_t *d_f = nullptr;
     double *d_w = nullptr;
     int64_t *d_steps = nullptr;
@@ -291,6 +292,8 @@ struct MultiWalk {
     int64_t count = 0;
 };
 cudaError_t launch_wilson_warp_multi(const MultiWalk &mw, cudaStream_t s);
+// resident one-warp blocks of the 32-walker kernel per SM (0 if the query fails)
+int wilson_warp_blocks_per_sm();
 
 // Batched multi-graph traversal / TTF: per-graph views and sub-wave buffers,
 // one entry (graph, tree of its sub-wave) per warp (or per grid row).

@@ -72,7 +72,7 @@ _STATS_FIELDS = [
     ("wf_sum", ctypes.c_double), ("w_sum", ctypes.c_double), ("x2_sum", ctypes.c_double),
     ("last_resistance", ctypes.c_double), ("last_cg_iters", ctypes.c_int64),
     ("traversal", ctypes.c_int32), ("tuned", ctypes.c_int32),
-    ("tune_ms", ctypes.c_double * 4),
+    ("tune_ms", ctypes.c_double * 4), ("resident_trees", ctypes.c_int64),
 ]
 
 

@@ -284,6 +284,7 @@ def test_step_cap_reports_error_and_keeps_handle():
 def test_seed_is_fixed_per_handle():
     g = S.cycle(10)
     with kc.KemenyGraph.from_graph(g) as G:
+        assert G.stats()["resident_trees"] > 0  # SMs x resident 32-walker blocks
         G.sample(5, 4)
         assert kc.STATUS[kc.kc_sample(G.h, 6, 4, check=False)] == "KC_ERR_INVALID_ARG"
         G.sample(5, 4)
