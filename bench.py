@@ -110,6 +110,13 @@ def algorithmic_bytes(phase: str, n: int, ecc: int, trees: int, steps: int) -> f
     return 0.0
 
 
+def path_bytes(n: int, ecc: int, bit: bool, trees: int, steps: int) -> float:
+    """Algorithmic bytes of the whole sampling path for `trees` trees with
+    `steps` Wilson departures in all: walk, traversal and f(tau)."""
+    ttf = "ttf_bit" if bit else "ttf_scan"
+    return sum(algorithmic_bytes(ph, n, ecc, trees, steps) for ph in ("wilson", "traverse", ttf))
+
+
 def dist_setup():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -529,7 +536,12 @@ def main():
                      "traffic_basis": None if traffic is None else
                      "ncu dram bytes per departure on grid300x300 (1000 trees) x departures",
                      "algorithmic_bytes_per_launch": per_launch_bytes,
-                     "mean_launch_ms": per_launch_s * 1000.0},
+                     "mean_launch_ms": per_launch_s * 1000.0,
+                     # the whole sampling path over the timed steps (walk,
+                     # traversal, f), against the same peak
+                     "path_frac": path_bytes(n, st["ecc"], st["ttf_variant"] == kc.KC_TTF_BIT,
+                                             trees_timed, steps_total)
+                                  / (tot_ms / 1000.0) / 1e9 / peak},
         "phase_ms": phase_ms,
         "steps_per_tree": steps_total / trees_timed,
         "gpu_launches": int(launches),
@@ -556,9 +568,14 @@ def main():
         t = time.perf_counter()
         k_hat = H.estimate(args.eps, args.delta)
         tte = time.perf_counter() - t
+        sh = H.stats()
+        drawn = H.samples(0, sh["pool_trees"])
+        tte_bytes = path_bytes(n, sh["ecc"], sh["ttf_variant"] == kc.KC_TTF_BIT,
+                               sh["pool_trees"], int(drawn["steps"].sum()))
         out["time_to_eps"] = {"value": tte, "unit": "s", "eps": args.eps, "delta": args.delta,
-                              "trees": H.stats()["pool_trees"], "K": k_hat,
+                              "trees": sh["pool_trees"], "K": k_hat,
                               "batch_trees": int(cfg2.batch_trees),
+                              "roofline_frac": tte_bytes / tte / 1e9 / peak,
                               "rule": "CLT: z s/sqrt(w) <= eps K (1-eps)"}
         H.close()
 

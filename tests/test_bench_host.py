@@ -24,6 +24,11 @@ def test_algorithmic_bytes_model():
         32 * (3 * lg + 4) * n * trees
     assert bench.algorithmic_bytes("ttf_scan", n, 7, trees, steps) == 32 * 2 * 7 * n * trees
     assert bench.algorithmic_bytes("other", n, 7, trees, steps) == 0.0
+    # the whole path: walk + traversal + the f variant in use
+    assert bench.path_bytes(n, 5, True, trees, steps) == \
+        32 * (2 * steps + 3 * n * trees) + 32 * 6 * n * trees + 32 * (3 * lg + 4) * n * trees
+    assert bench.path_bytes(n, 7, False, trees, steps) == \
+        32 * (2 * steps + 3 * n * trees) + 32 * 6 * n * trees + 32 * 2 * 7 * n * trees
 
 
 def test_serving_workload_is_seeded_and_mixed():
