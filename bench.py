@@ -199,14 +199,15 @@ def host_cpu_model(cpuinfo: str = "/proc/cpuinfo") -> str:
 
 
 def single_core_baseline(g, seed: int, budget_s: float = 5.0) -> dict:
-    """The oracle on one core: a small calibration batch, then about
-    `budget_s` seconds of trees."""
-    trees = 2
-    _, el, _ = oracle_baseline(g, trees, seed, threads=1)
-    if el < budget_s / 2:
-        more = int(min(1 << 20, max(1, trees * (budget_s - el) / max(el, 1e-3))))
-        _, el2, _ = oracle_baseline(g, more, seed, threads=1, first=trees)
-        trees, el = trees + more, el + el2
+    """The oracle on one core: a small calibration batch, then batches sized
+    from the rate seen so far until about `budget_s` seconds of trees."""
+    trees, el, batch = 0, 0.0, 2
+    for _ in range(4):
+        _, e, _ = oracle_baseline(g, batch, seed, threads=1, first=trees)
+        trees, el = trees + batch, el + e
+        if el >= budget_s / 2:
+            break
+        batch = int(min(1 << 20, max(1, batch / max(e, 1e-3) * (budget_s - el))))
     return {"value": trees / el, "unit": "trees/s", "cores": 1,
             "sample": f"{trees} trees (sample ids 0..{trees - 1}), {el:.1f} s"}
 
@@ -615,15 +616,20 @@ def main():
 
     # ---- the CPU oracle on the host cores (rank 0, N = 1 only)
     if not args.no_cpu_baseline and rank == 0 and ws == 1:
-        # a calibration batch, then enough further trees for about 15 s of work
-        cores = os.cpu_count() or 1
-        trees = max(2 * cores, 16)
-        _, el, used = oracle_baseline(g, trees, args.seed)
-        if el < 10.0:
-            more = int(min(1 << 22, max(cores, trees * (15.0 - el) / max(el, 1e-3))))
-            more = (more + cores - 1) // cores * cores
-            _, el2, used = oracle_baseline(g, more, args.seed, first=trees)
-            trees, el = trees + more, el + el2
+        # a calibration batch, then batches sized from the rate seen so far
+        # until about 15 s of work (small batches overstate the per-tree time,
+        # so one correction may not reach it)
+        cores = host_cores()
+        trees, el, used = 0, 0.0, cores
+        batch = max(2 * cores, 16)
+        for _ in range(4):
+            _, e, used = oracle_baseline(g, batch, args.seed, first=trees)
+            trees, el = trees + batch, el + e
+            if el >= 10.0:
+                break
+            rate = batch / max(e, 1e-3)
+            batch = int(min(1 << 22, max(cores, rate * (15.0 - el))))
+            batch = (batch + cores - 1) // cores * cores
         out["cpu_baseline"] = {"value": trees / el, "unit": "trees/s", "cores": used,
                                "kind": "oracle",
                                "sample": f"{trees} trees (sample ids 0..{trees - 1}) of "
