@@ -13,14 +13,17 @@ by cycle popping the model must reproduce the oracle's sequential tree, step
 count and depths for every start order and walker count.  It documents and
 checks the protocol's design on the CPU; it is not the device code.
 
-    python tests/walker_protocol_model.py 100 64   # tail study: grid side, trees
+    python tests/walker_protocol_model.py 100 64        # tail study: grid side, trees
+    python tests/walker_protocol_model.py phases 120 300 # waits and departures per iteration
 """
 import numpy as np
 
 IDLE, WALK, WAIT, POPSET, POP, COUNT, COMMIT, DONE = range(8)
 
 
-def walk_tree(g, r, seed, sample, sorder, lanes=32, max_iter=10 ** 7):
+def walk_tree(g, r, seed, sample, sorder, lanes=32, max_iter=10 ** 7, phases=None):
+    """phases: optional list of 8 counters, incremented per lane-iteration
+    spent in each phase (IDLE .. DONE)."""
     import oracle as O
 
     n = g.n
@@ -66,6 +69,9 @@ def walk_tree(g, r, seed, sample, sorder, lanes=32, max_iter=10 ** 7):
         if all(p == DONE for p in ph):
             break
         # act: departures and the vertex each lane reads
+        if phases is not None:
+            for p in ph:
+                phases[p] += 1
         ld = [-1] * L
         for lane in range(L):
             p = ph[lane]
@@ -251,10 +257,31 @@ def tail_study(side: int, trees: int, lanes_list=(32, 128)):
               f"ratio {it[slow] / it[med]:.1f}")
 
 
+def phase_study(sides, lanes: int = 32):
+    """Departures per iteration and the share of lane-iterations spent waiting
+    on another walker's path, for one tree on each perturbed grid."""
+    import oracle as O
+    from paper_2511_16356_gb300 import synth as S
+
+    for side in sides:
+        g = S.grid_perturbed(side, side, 0.25, 1)
+        t0 = O.tau0(g)
+        sorder = np.random.default_rng(0).permutation(g.n)
+        counts = [0] * 8
+        _, st, _, _, it = walk_tree(g, t0.r, 5, 0, sorder, lanes=lanes, phases=counts)
+        busy = sum(counts) - counts[DONE]
+        print(f"{side}x{side} grid, {lanes} lanes: {st / it:.2f} departures per iteration, "
+              f"{counts[WAIT] / busy:.0%} of lane-iterations waiting, "
+              f"{counts[WALK] / busy:.0%} walking", flush=True)
+
+
 if __name__ == "__main__":
     import os
     import sys
 
     sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
-    tail_study(int(sys.argv[1]) if len(sys.argv) > 1 else 100,
-               int(sys.argv[2]) if len(sys.argv) > 2 else 64)
+    if len(sys.argv) > 1 and sys.argv[1] == "phases":
+        phase_study([int(a) for a in sys.argv[2:]] or [60, 120])
+    else:
+        tail_study(int(sys.argv[1]) if len(sys.argv) > 1 else 100,
+                   int(sys.argv[2]) if len(sys.argv) > 2 else 64)
