@@ -30,7 +30,7 @@ from statistics import NormalDist
 
 import numpy as np
 
-__all__ = ["z_upper", "EstimateRun", "estimate_clt", "estimate_fixed"]
+__all__ = ["z_upper", "EstimateRun", "estimate_clt", "estimate_fixed", "accepted_samples"]
 
 
 def z_upper(p: float) -> float:
@@ -103,3 +103,34 @@ def estimate_clt(draw, twom: int, eps: float, delta: float, batch: int = 1024,
         more(count)
     return EstimateRun(K=estimate_fixed(f, twom), trees=len(f), rounds=rounds, margin=margin,
                        sizes=sizes)
+
+
+def accepted_samples(sample, cap: int, count: int, id0: int = 0, block: int = 1024):
+    """Sampling with rejection by walk length: the first `count` sample ids,
+    from id0 on, whose Wilson step count is at most `cap`, with their f and
+    step counts.  sample(first, k) returns (f, steps) of ids first .. first+k-1.
+
+    Rejection by step count leaves the accepted trees uniform.  Give every
+    vertex a stack of independent uniform arrows; Wilson's walks pop cycles of
+    arrows until the arrows on top form a tree T rooted at r (Sec. 2.2, with
+    the cycle-popping view of Wilson's algorithm).  The probability that the
+    popped cycles are C and the final tree is T is the product of the
+    probabilities of the arrows involved: a factor for C times the product of
+    1/d(v) over the non-root vertices, which is the same for every tree.  So T
+    is uniform and independent of C, and the step count -- every popped arrow
+    plus one arrow per non-root vertex -- is a function of C alone.  Any rule
+    that accepts a tree according to its step count therefore keeps f(T)/2m an
+    unbiased sample of K (Theorem 3)."""
+    ids, fs, ss = [], [], []
+    first = id0
+    while len(ids) < count:
+        f, steps = sample(first, block)
+        for k in range(block):
+            if steps[k] <= cap:
+                ids.append(first + k)
+                fs.append(int(f[k]))
+                ss.append(int(steps[k]))
+                if len(ids) == count:
+                    break
+        first += block
+    return np.array(ids, dtype=np.int64), np.array(fs, dtype=np.int64), np.array(ss, dtype=np.int64)
