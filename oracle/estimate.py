@@ -34,8 +34,9 @@ __all__ = ["z_upper", "EstimateRun", "estimate_clt", "estimate_fixed", "accepted
 
 
 def z_upper(p: float) -> float:
-    """z with P(Z > z) = p for a standard normal Z."""
-    return NormalDist().inv_cdf(1.0 - p)
+    """z with P(Z > z) = p for a standard normal Z (by symmetry, minus the
+    lower p-quantile: 1 - p would round small tails away)."""
+    return -NormalDist().inv_cdf(p)
 
 
 @dataclass

@@ -18,6 +18,7 @@
 
 #include "kc_common.cuh"
 #include "kc_host_graph.h"
+#include "kc_host_stop.h"
 
 namespace kc {
 cudaError_t launch_out_from_size(int64_t n, const int32_t *din, const int32_t *size,
@@ -1079,17 +1080,6 @@ void apply_delete(kc_graph *g, int32_t u, int32_t v, int32_t mode) {
     if (g->cfg.refresh_after_update || tau0_hit) refresh_slots(g, all_slots(g));
 }
 
-double inv_normal_upper(double p_upper) {
-    // z with P(Z > z) = p_upper, by bisection on erfc (monotone)
-    double lo = -40.0, hi = 40.0;
-    for (int i = 0; i < 200; ++i) {
-        const double mid = 0.5 * (lo + hi);
-        const double tail = 0.5 * std::erfc(mid / std::sqrt(2.0));
-        if (tail > p_upper) lo = mid; else hi = mid;
-    }
-    return 0.5 * (lo + hi);
-}
-
 double i128_to_double(long long hi, unsigned long long lo) {
     return std::ldexp((double)hi, 64) + (double)lo;
 }
@@ -1768,30 +1758,15 @@ kc_status kc_estimate(kc_graph *g, double eps, double delta, double *K_out) {
         const int64_t batch = g->cfg.batch_trees > 0 ? g->cfg.batch_trees : 1024;
         if (eps > 0) {
             if (g->cfg.stop_rule == KC_STOP_HOEFFDING) {
-                const double nn = (double)g->n, mm = (double)g->m, e = (double)g->ecc;
-                const double kmin = (nn - 1) * (nn - 1) / nn;
-                const double need = std::ceil(8.0 * mm * mm * e * e * std::log(2.0 / delta) /
-                                              (kmin * kmin * eps * eps));
-                const int64_t want = (int64_t)std::min<double>(need, (double)cap);
+                const int64_t want = kc_host::hoeffding_trees(g->n, g->m, g->ecc, eps, delta, cap);
                 if (want > g->pool) do_sample(g, want - g->pool);
             } else {
-                const double z = inv_normal_upper(delta / 2.0);
-                if (g->pool < 64) do_sample(g, std::max<int64_t>(64, std::min(batch, cap)) - g->pool);
-                for (int iter = 0; iter < 64; ++iter) {
-                    PoolSums s = reduce_pool(g);
-                    const double w = (double)s.count;
-                    const double mean = s.wf / s.w;
-                    const double var = std::max(0.0, (s.x2 - w * mean * mean) / std::max(1.0, w - 1.0));
-                    const double sd = std::sqrt(var);
-                    const double tol = eps * mean * (1.0 - eps);
-                    if (w >= 64 && z * sd / std::sqrt(w) <= tol) break;
-                    if (g->pool >= cap) break;
-                    double need = tol > 0 ? std::ceil((z * sd / tol) * (z * sd / tol)) : (double)cap;
-                    int64_t more = (int64_t)std::min<double>(std::max<double>(need - w, (double)batch),
-                                                             (double)(cap - g->pool));
-                    if (more <= 0) break;
-                    do_sample(g, more);
-                }
+                kc_host::run_clt(
+                    delta, eps, batch, cap, g->pool, [&](int64_t k) { do_sample(g, k); },
+                    [&] {
+                        const PoolSums s = reduce_pool(g);
+                        return kc_host::Moments{s.count, s.wf, s.w, s.x2};
+                    });
             }
         }
         if (g->pool == 0) {
