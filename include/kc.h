@@ -130,7 +130,10 @@ typedef struct {
     int64_t max_trees_in_flight; /* 0: chosen from free device memory               */
     int64_t batch_trees;        /* kc_estimate batch size (0: 1024)                 */
     int64_t max_trees;          /* kc_estimate cap on the pool size (0: 1 << 24)     */
-    int64_t step_cap;           /* per-tree cap on Wilson steps (0: max(2^22, 1024 n)) */
+    int64_t step_cap;           /* cap on Wilson departures (0: max(2^22, 1024 n)), per
+                                   tree for the one-walker kernel and per walker for
+                                   the 32-walker kernel (a tree may then take up to
+                                   32 x step_cap); exceeding it is KC_ERR_STEP_LIMIT */
     double mem_fraction;        /* share of free device memory for workspaces (0: 0.8) */
     int64_t sample_id_base;     /* first sample id of the pool (0); ranks of a
                                    multi-GPU run use disjoint bases, ids < 2^32   */

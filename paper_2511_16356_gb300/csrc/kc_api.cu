@@ -278,9 +278,10 @@ void ensure_stack(kc_graph *g, Plan &p, uint32_t maxdepth, cudaStream_t st = nul
     p.stack_cap = need_cap;
 }
 
-// Per-tree cap on Wilson departures: the configured value, or
-// max(2^22, 1024 n) (about 60 times the mean step count of a road-shaped
-// graph, far above that of low-diameter graphs).
+// Cap on Wilson departures (per tree for the one-walker kernel, per walker for
+// the 32-walker kernel): the configured value, or max(2^22, 1024 n) (about 60
+// times the mean step count of a road-shaped graph, far above that of
+// low-diameter graphs).
 int64_t step_cap_of(const kc_graph *g) {
     if (g->cfg.step_cap > 0) return g->cfg.step_cap;
     return std::max<int64_t>((int64_t)1 << 22, 1024 * g->n);
