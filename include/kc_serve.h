@@ -34,7 +34,7 @@ typedef struct kc_server kc_server; /* opaque */
 typedef struct {
     uint32_t struct_size;   /* sizeof(kc_server_config), for ABI growth                  */
     int32_t workers;        /* requests in flight at once: host threads, one CUDA stream
-                               each (0: 4)                                              */
+                               each (0: 4; at most 64)                                  */
     int64_t budget_bytes;   /* device bytes shared by the workspaces of in-flight
                                requests (0: half the free device memory at creation)    */
     int64_t request_bytes;  /* workspace cap of one request (0: budget / workers); a
@@ -69,7 +69,8 @@ kc_status kc_server_create(const kc_server_config *cfg, kc_server **out);
 kc_status kc_server_destroy(kc_server *s);
 
 /*
- * Make a graph resident (kc_graph_create semantics for n, row_off, col, cfg).
+ * Make a graph resident (kc_graph_create semantics for n, row_off, col, cfg,
+ * except that cfg->keep_trees is replaced: 1 for a dynamic graph, else 0).
  * pool_trees > 0 makes it a dynamic graph: a pool of that many trees is drawn
  * under pool_seed (trees retained) and serves POOL_QUERY and UPDATE; otherwise
  * it serves QUERY.  *graph_id receives the id (0, 1, ...).
