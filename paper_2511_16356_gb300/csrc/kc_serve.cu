@@ -15,6 +15,7 @@
 #include <cuda_runtime.h>
 
 #include "../../include/kc_serve.h"
+#include "kc_host_admit.h"
 
 namespace {
 
@@ -65,25 +66,18 @@ struct kc_server {
         return want < cfg.request_bytes ? want : cfg.request_bytes;
     }
 
-    // the first waiting request that may start now: its graph idle, no earlier
-    // waiting request on the same graph, and its reservation fits the budget
-    // (later requests may pass one that does not fit yet)
+    // the first waiting request that may start now (kc_host_admit.h)
     bool pick(int64_t *ticket, int64_t *bytes) {
-        std::vector<char> seen(graphs.size(), 0);
-        for (auto it = queue.begin(); it != queue.end(); ++it) {
-            Request &r = *reqs[(size_t)*it];
-            if (seen[(size_t)r.graph]) continue;
-            seen[(size_t)r.graph] = 1;
-            Graph &g = graphs[(size_t)r.graph];
-            if (g.busy) continue;
-            const int64_t b = reserve_for(g);
-            if (reserved + b > cfg.budget_bytes && reserved > 0) continue;
-            *ticket = *it;
-            *bytes = b;
-            queue.erase(it);
-            return true;
-        }
-        return false;
+        auto it = kc_host::first_admissible(
+            queue.begin(), queue.end(), graphs.size(),
+            [&](int64_t t) { return reqs[(size_t)t]->graph; },
+            [&](size_t gi) { return graphs[gi].busy; },
+            [&](size_t gi) { return reserve_for(graphs[gi]); }, reserved, cfg.budget_bytes,
+            bytes);
+        if (it == queue.end()) return false;
+        *ticket = *it;
+        queue.erase(it);
+        return true;
     }
 
     void run(int wid) {
