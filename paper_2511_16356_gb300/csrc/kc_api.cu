@@ -19,6 +19,7 @@
 #include "kc_common.cuh"
 #include "kc_host_graph.h"
 #include "kc_host_stop.h"
+#include "kc_host_plan.h"
 
 namespace kc {
 cudaError_t launch_out_from_size(int64_t n, const int32_t *din, const int32_t *size,
@@ -102,30 +103,10 @@ struct Phase {
 };
 
 // Workspace carving ----------------------------------------------------------
-struct Plan {
-    int64_t BW = 0;        // trees per Wilson wave
-    int64_t BT = 0;        // trees per traversal sub-wave
-    bool bit = false;
-    int64_t stack_cap = 0; // BIT stack entries per tree
-    bool canon = true;     // sub-wave buffers for the id-ordered DFN (aux array)
-};
+using kc_host::Plan;
+using kc_host::align256;
 
-size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
-
-size_t ws_size(const kc_graph *g, const Plan &p) {
-    const size_t n = (size_t)g->n;
-    size_t b = 0;
-    b += align256(sizeof(uint64_t) * n * p.BW);      // word
-    b += align256(sizeof(int32_t) * n * p.BW);       // ord
-    b += 3 * align256(sizeof(int64_t) * p.BW);       // steps, f, sids
-    b += 2 * align256(sizeof(int32_t) * p.BW) + 256;  // hybrid hand-off: rs_q, rs_pos, done
-    b += align256(sizeof(int32_t) * n * p.BT);       // size
-    b += align256(sizeof(int64_t) * n * p.BT);       // vol
-    b += align256(sizeof(int32_t) * n * p.BT);       // din
-    if (p.bit || p.canon) b += align256(sizeof(int32_t) * n * p.BT);  // aux
-    if (p.bit) b += align256(sizeof(int64_t) * (n + 1) * p.BT);  // bit
-    return b;
-}
+size_t ws_size(const kc_graph *g, const Plan &p) { return kc_host::ws_bytes(g->n, p); }
 
 struct Carved {
     WaveView wv;       // Wilson-wave view (B = BW), traversal fields point at sub-wave buffers
@@ -222,44 +203,16 @@ void ensure_pool(kc_graph *g, int64_t need) {
     g->h_modified.resize((size_t)cap, 0);
 }
 
-// Trees per Wilson wave (BW: walker words and parent-first order, 12 bytes a
-// vertex) and per traversal sub-wave (BT: sizes, volumes, DFN, and for BIT the
-// preorder and the BIT itself).  Low-eccentricity graphs (SCAN) spend more time
-// in the traversal than in Wilson, so both get the same count; long-diameter
-// graphs (BIT) spend most of it in Wilson, which gets 70% of the budget.
+// Wave sizes within the workspace budget (kc_host_plan.h): the handle's cap,
+// or a share of the device's free memory (counting the workspace it holds).
 Plan plan_for(kc_graph *g, int64_t ntrees, bool canon = true) {
-    Plan p;
-    p.bit = g->ttf_variant == KC_TTF_BIT;
-    p.canon = canon;
     size_t free_b = 0, total_b = 0;
     KC_CK(g, cudaMemGetInfo(&free_b, &total_b));
     const double frac = g->cfg.mem_fraction > 0 ? g->cfg.mem_fraction : 0.8;
     const double budget = g->ws_limit > 0 ? (double)g->ws_limit
                                           : (double)(free_b + g->ws_bytes) * frac;
-    const double n = (double)g->n;
-    const double per_w = 12.0 * n + 64.0 + 8.0;
-    const double per_t = (p.bit ? 28.0 : (canon ? 20.0 : 16.0)) * n + 64.0 +
-                         (p.bit ? 16.0 * 4096.0 : 0.0);
-    int64_t bw, bt;
-    if (p.bit) {
-        bw = (int64_t)std::floor(0.7 * budget / per_w);
-        bw = std::max<int64_t>(1, std::min<int64_t>(bw, ntrees));
-        if (g->cfg.max_trees_in_flight > 0) bw = std::min(bw, g->cfg.max_trees_in_flight);
-        bw = std::min<int64_t>(bw, 1 << 20);
-        bt = (int64_t)std::floor((budget - (double)bw * per_w) / per_t);
-    } else {
-        bw = (int64_t)std::floor(budget / (per_w + per_t));
-        bw = std::max<int64_t>(1, std::min<int64_t>(bw, ntrees));
-        if (g->cfg.max_trees_in_flight > 0) bw = std::min(bw, g->cfg.max_trees_in_flight);
-        bw = std::min<int64_t>(bw, 1 << 20);
-        bt = bw;
-    }
-    bt = std::max<int64_t>(1, std::min<int64_t>(bt, bw));
-    bt = std::min<int64_t>(bt, 65535);
-    p.BW = bw;
-    p.BT = bt;
-    p.stack_cap = p.bit ? 4096 : 0;
-    return p;
+    return kc_host::plan_waves(g->n, ntrees, g->ttf_variant == KC_TTF_BIT, canon, budget,
+                               g->cfg.max_trees_in_flight);
 }
 
 // DFS stack of the BIT variant: one entry per stacked ancestor, so the
