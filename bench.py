@@ -305,6 +305,77 @@ def batched_leg(args, kc):
             "identical_results": all(np.array_equal(a, b) for a, b in zip(f_b, f_s))}
 
 
+def update_stream(g, n_updates: int, bmax: int, seed: int = 4):
+    """Seeded edge-update batches against the evolving graph: half insertions of
+    absent pairs, half deletions of edges that lie on a triangle (never a
+    bridge), batch sizes uniform on [1, bmax]."""
+    rng = np.random.default_rng(seed)
+    adj = [set(g.col[g.row_off[v]:g.row_off[v + 1]].tolist()) for v in range(g.n)]
+    edges = [tuple(e) for e in g.edges().tolist()]
+    batches, done = [], 0
+    while done < n_updates:
+        b = int(min(rng.integers(1, bmax + 1), n_updates - done))
+        ops = []
+        while len(ops) < b:
+            if rng.random() < 0.5:
+                u, v = (int(x) for x in rng.choice(g.n, 2, replace=False))
+                if v in adj[u]:
+                    continue
+                adj[u].add(v)
+                adj[v].add(u)
+                edges.append((min(u, v), max(u, v)))
+                ops.append((u, v, 0))
+            else:
+                k = int(rng.integers(len(edges)))
+                u, v = edges[k]
+                if v not in adj[u] or not (adj[u] & adj[v]):
+                    continue
+                adj[u].discard(v)
+                adj[v].discard(u)
+                edges[k] = edges[-1]
+                edges.pop()
+                ops.append((u, v, 1))
+        batches.append(ops)
+        done += b
+    return batches
+
+
+def dynamic_leg(args, kc):
+    """Sample maintenance under a stream of update batches with a Kemeny query
+    after each batch: ISM against BSM on the same pool and stream."""
+    from paper_2511_16356_gb300 import synth as S
+
+    g = S.chung_lu(args.dyn_n, 2.1, 20.0, 4)
+    batches = update_stream(g, args.dyn_updates, args.dyn_batch)
+    out = {"workload": f"Chung-Lu gamma 2.1, mean degree 20, seed 4 (n = {g.n:,}, m = {g.m:,}); "
+                       f"{args.dyn_updates} updates in {len(batches)} batches of 1-"
+                       f"{args.dyn_batch}, half insertions, half deletions of triangle edges; "
+                       f"pool of {args.dyn_trees} trees; a query at eps {args.eps} after "
+                       f"each batch"}
+    for name, mode in (("ism", kc.KC_UPDATE_ISM), ("bsm", kc.KC_UPDATE_BSM)):
+        cfg = kc.kc_config_default()
+        cfg.keep_trees = 1
+        G = kc.KemenyGraph.from_graph(g, cfg)
+        G.sample(args.seed, args.dyn_trees)
+        upd_s, q_ms = 0.0, []
+        k_hat = 0.0
+        for ops in batches:
+            t = time.perf_counter()
+            G.update(ops, mode)
+            upd_s += time.perf_counter() - t
+            t = time.perf_counter()
+            k_hat = G.estimate(args.eps, args.delta)
+            q_ms.append(1000.0 * (time.perf_counter() - t))
+        st = G.stats()
+        G.close()
+        out[name] = {"update_ms_per_op": 1000.0 * upd_s / max(1, args.dyn_updates),
+                     "query_p50_ms": float(np.percentile(q_ms, 50)),
+                     "query_p99_ms": float(np.percentile(q_ms, 99)),
+                     "trees_resampled": int(st["trees_resampled"]),
+                     "pool_trees": int(st["pool_trees"]), "K_final": k_hat}
+    return out
+
+
 def serve_leg(args, kc):
     """Served (continuous batching, `--serve-workers` streams) against the plain
     one-graph-per-call path on the same Poisson stream of Kemeny queries."""
@@ -425,6 +496,12 @@ def main():
                     help="trees per graph in the batched multi-graph leg")
     ap.add_argument("--serve-load", type=float, default=1.5,
                     help="offered query rate as a multiple of the plain path's capacity")
+    ap.add_argument("--dynamic", action="store_true",
+                    help="also run the update-stream leg (ISM against BSM)")
+    ap.add_argument("--dyn-n", type=int, default=100000)
+    ap.add_argument("--dyn-updates", type=int, default=1000)
+    ap.add_argument("--dyn-batch", type=int, default=100)
+    ap.add_argument("--dyn-trees", type=int, default=1000)
     args = ap.parse_args()
     if args.warmup < 3:
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
@@ -613,6 +690,10 @@ def main():
     if not args.no_serve and rank == 0:
         out["serve"] = serve_leg(args, kc)
         out["batched"] = batched_leg(args, kc)
+
+    # ---- sample maintenance under an update stream (rank 0, on request)
+    if args.dynamic and rank == 0:
+        out["dynamic"] = dynamic_leg(args, kc)
 
     # ---- the CPU oracle on the host cores (rank 0, N = 1 only)
     if not args.no_cpu_baseline and rank == 0 and ws == 1:

@@ -92,3 +92,45 @@ def test_reference_arm_under_torchrun_two_ranks():
     d = json.loads(lines[0])
     assert d["impl"] == "reference" and d["n_gpus"] == 2 and d["value"] > 0
     assert d["cpu_baseline"]["cores"] == bench.host_cores()
+
+
+def test_update_stream_is_valid_against_the_evolving_graph():
+    """Every insertion adds an absent edge and every deletion removes a present
+    edge that is not a bridge (the graph stays connected); the stream is
+    seeded and has the requested size."""
+    from collections import deque
+
+    from paper_2511_16356_gb300 import synth as S
+
+    g = S.chung_lu(400, 2.1, 6.0, 4)
+    a = bench.update_stream(g, 300, 40, seed=4)
+    b = bench.update_stream(g, 300, 40, seed=4)
+    assert a == b and sum(len(x) for x in a) == 300 and max(len(x) for x in a) <= 40
+    adj = [set(g.col[g.row_off[v]:g.row_off[v + 1]].tolist()) for v in range(g.n)]
+
+    def connected(u, v):
+        seen, q = {u}, deque([u])
+        while q:
+            x = q.popleft()
+            if x == v:
+                return True
+            for y in adj[x]:
+                if y not in seen:
+                    seen.add(y)
+                    q.append(y)
+        return False
+
+    kinds = set()
+    for batch in a:
+        for u, v, op in batch:
+            kinds.add(op)
+            if op == 0:
+                assert u != v and v not in adj[u]
+                adj[u].add(v)
+                adj[v].add(u)
+            else:
+                assert v in adj[u]
+                adj[u].discard(v)
+                adj[v].discard(u)
+                assert connected(u, v)
+    assert kinds == {0, 1}
