@@ -20,6 +20,10 @@ guarantee through the normal approximation of the sample mean:
 Sums here are exact integers (Python ints and fractions), converted to floating
 point only for the comparison and the square root, so each decision is the
 exact one; ``margin`` reports how far the closest decision was from flipping.
+
+``accepted_samples`` draws with rejection by walk length: trees whose Wilson
+step count exceeds a cap are skipped, which leaves the accepted ones uniform
+(its docstring gives the argument).
 """
 from __future__ import annotations
 
