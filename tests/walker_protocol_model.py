@@ -252,9 +252,10 @@ def tail_study(side: int, trees: int, lanes_list=(32, 128)):
     print(f"{side}x{side} grid, {trees} trees: slowest S / median S = {steps[slow] / steps[med]:.2f}")
     for L in lanes_list:
         it = np.array(its[L])
+        alpha = np.polyfit(np.log(steps), np.log(it), 1)[0]  # iterations ~ S^alpha
         print(f"  {L} lanes: slowest tree {it[slow]} iterations ({steps[slow] / it[slow]:.1f} "
               f"departures each), median tree {it[med]} ({steps[med] / it[med]:.1f}); "
-              f"ratio {it[slow] / it[med]:.1f}")
+              f"ratio {it[slow] / it[med]:.1f}; iterations ~ S^{alpha:.2f} over the trees")
 
 
 def phase_study(sides, lanes: int = 32):
