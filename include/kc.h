@@ -147,6 +147,14 @@ typedef struct {
     int32_t tau0_kind;          /* KC_TAU0_*: the path tree (kc_update needs BFS)    */
     int32_t reserved1;
     uint64_t tau0_seed;         /* seed of the KC_TAU0_WILSON path tree              */
+    int64_t reject_steps;       /* > 0: rejection by walk length.  A tree whose
+                                   Wilson step count exceeds this is abandoned and
+                                   the next sample id drawn instead, so the pool holds
+                                   the first accepted ids (not consecutive).  The
+                                   tree is independent of its step count, so the
+                                   accepted trees stay uniform.  Needs the 32-walker
+                                   kernel, keep_trees = 0 and no autotune; not for
+                                   kc_sample_multi.  0: off (default)               */
 } kc_config;
 
 /* Fill *cfg with the defaults listed above. */
@@ -314,6 +322,7 @@ typedef struct {
     double tune_ms[4];           /* autotuner pilots: walk ms per tree (32 walkers,
                                    1 walker), traversal ms per tree (chunked,
                                    leaf-to-root); 0 when not measured              */
+    int64_t trees_rejected;      /* trees abandoned by rejection by walk length  */
     int64_t resident_trees;      /* trees the 32-walker kernel runs at once on this
                                    GPU (SMs x resident one-warp blocks).  A wave of
                                    up to this many trees lasts about as long as its

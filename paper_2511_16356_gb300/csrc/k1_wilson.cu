@@ -241,8 +241,11 @@ enum : int {
 // kMulti: block j walks tree mw.entry[j].y of graph mw.entry[j].x, every graph
 // with its own view, wave, seed, sample ids, start order and step cap (the
 // batched multi-graph launch); otherwise one graph and wave as passed.
+// kReject: step_cap bounds the tree's total departures (the warp's sum), and a
+// tree that exceeds it is abandoned and marked steps = -1 instead of failing the
+// wave (rejection by walk length, which keeps the accepted trees uniform).
 constexpr int kWarpWalkerBlock = 32;
-template <bool kMulti>
+template <bool kMulti, bool kReject>
 __global__ void __launch_bounds__(kWarpWalkerBlock, 24)
     k_wilson_warp(GraphView g_in, WaveView w_in, uint64_t seed_in,
                   const int64_t *__restrict__ sids_in, const int32_t *__restrict__ sorder_in,
@@ -298,6 +301,7 @@ __global__ void __launch_bounds__(kWarpWalkerBlock, 24)
     int64_t next_start = rs_q ? (int64_t)rs_q[t] : 0;  // warp-uniform
     int64_t pos = rs_q ? (int64_t)rs_pos[t] : w.pos0;   // warp-uniform, ord[0 .. pos) placed
     bool bad = false;
+    bool rejected = false;  // warp-uniform
 
     for (int64_t it = 0;; ++it) {
         // ---- hand out start vertices to idle lanes
@@ -317,6 +321,19 @@ __global__ void __launch_bounds__(kWarpWalkerBlock, 24)
             if (lane == 0) atomicOr(w.err, bad ? kErrBadTree : kErrIterLimit);
             break;
         }
+        if constexpr (kReject) {
+            // every 8th iteration: abandon the tree once its departures pass
+            // the cap (the final count is checked again at the end)
+            if ((it & 7) == 0) {
+                long long tt = (long long)steps;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) tt += __shfl_xor_sync(kFull, tt, o);
+                if (tt > step_cap) {
+                    rejected = true;
+                    break;
+                }
+            }
+        }
         // ---- act: departures and the address each lane reads this iteration
         int32_t ld = -1;
         if (ph == pWalk) {
@@ -328,7 +345,7 @@ __global__ void __launch_bounds__(kWarpWalkerBlock, 24)
             ++steps;
             x = v;
             ld = v;
-            if (cc >= kCountMask || steps > step_cap) {
+            if (cc >= kCountMask || (!kReject && steps > step_cap)) {
                 atomicOr(w.err, kErrStepLimit);
                 bad = true;
                 ph = pDone;
@@ -494,6 +511,12 @@ __global__ void __launch_bounds__(kWarpWalkerBlock, 24)
             }
         }
     }
+    if constexpr (kReject) {
+        if (rejected) {
+            if (lane == 0) w.steps[t] = -1;
+            return;
+        }
+    }
     long long tot = (long long)steps;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) tot += __shfl_down_sync(kFull, tot, o);
@@ -501,8 +524,12 @@ __global__ void __launch_bounds__(kWarpWalkerBlock, 24)
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) md = max(md, __shfl_down_sync(kFull, md, o));
     if (lane == 0) {
-        w.steps[t] = (rs_q ? w.steps[t] : 0) + tot;
-        atomicMax(w.maxdepth, md);
+        if (kReject && tot > step_cap) {
+            w.steps[t] = -1;  // finished between two checks, but past the cap
+        } else {
+            w.steps[t] = (rs_q ? w.steps[t] : 0) + tot;
+            atomicMax(w.maxdepth, md);
+        }
     }
     if (done_flag) {
         // publish the finished tree (its depth + 1) to the host, after every
@@ -524,14 +551,25 @@ cudaError_t launch_wilson_warp(const GraphView &g, WaveView w, uint64_t seed, co
     // a correct run needs at most about 3 iterations per departure (walk,
     // count, commit / pop), however the walkers serialise
     const int64_t iter_cap = 4 * step_cap + 64 * g.n + 4096;
-    k_wilson_warp<false><<<(unsigned)w.B, kWarpWalkerBlock, 0, s>>>(
+    k_wilson_warp<false, false><<<(unsigned)w.B, kWarpWalkerBlock, 0, s>>>(
         g, w, seed, sids, sorder, step_cap, iter_cap, rs_q, rs_pos, done_flag, MultiWalk{});
+    return cudaGetLastError();
+}
+
+cudaError_t launch_wilson_warp_reject(const GraphView &g, WaveView w, uint64_t seed,
+                                      const int64_t *sids, const int32_t *sorder,
+                                      int64_t tree_cap, cudaStream_t s) {
+    // tree_cap bounds the whole tree's departures, and an iteration may move
+    // as little as one lane: a generous bound that no accepted tree reaches
+    const int64_t iter_cap = 16 * std::min<int64_t>(tree_cap, (int64_t)1 << 40) + 64 * g.n + 4096;
+    k_wilson_warp<false, true><<<(unsigned)w.B, kWarpWalkerBlock, 0, s>>>(
+        g, w, seed, sids, sorder, tree_cap, iter_cap, nullptr, nullptr, nullptr, MultiWalk{});
     return cudaGetLastError();
 }
 
 int wilson_warp_blocks_per_sm() {
     int b = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_wilson_warp<false>, kWarpWalkerBlock,
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_wilson_warp<false, false>, kWarpWalkerBlock,
                                                       0) != cudaSuccess) {
         (void)cudaGetLastError();
         return 0;
@@ -541,7 +579,7 @@ int wilson_warp_blocks_per_sm() {
 
 cudaError_t launch_wilson_warp_multi(const MultiWalk &mw, cudaStream_t s) {
     if (mw.count <= 0) return cudaSuccess;
-    k_wilson_warp<true><<<(unsigned)mw.count, kWarpWalkerBlock, 0, s>>>(
+    k_wilson_warp<true, false><<<(unsigned)mw.count, kWarpWalkerBlock, 0, s>>>(
         GraphView{}, WaveView{}, 0, nullptr, nullptr, 0, 0, nullptr, nullptr, nullptr, mw);
     return cudaGetLastError();
 }

@@ -1100,8 +1100,128 @@ void autotune(kc_graph *g, Plan &p, int64_t B, int64_t sid0) {
     g->tuned = true;
 }
 
+// Rejection by walk length: waves of the 32-walker kernel abandon trees past
+// cfg.reject_steps departures; each wave's accepted trees are traversed and
+// evaluated through a tree map and appended to the pool in sample-id order,
+// until ntrees are accepted.  Rejected ids are consumed (never reused).
+void do_sample_reject(kc_graph *g, int64_t ntrees) {
+    ensure_pool(g, g->pool + ntrees);
+    Plan p = plan_for(g, ntrees, false);
+    ensure_ws(g, p);
+    ensure_pipeline(g, p.BW);  // tree-map staging: h_map / d_map
+    const int64_t pool0 = g->pool, sid_base = g->next_sid;
+    const GraphView gv = view_of(g);
+    try {
+        int64_t accepted = 0;
+        while (accepted < ntrees) {
+            if (g->next_sid - sid_base > 64 * ntrees + 4096) {
+                g->last_error = "rejection by walk length accepts too few trees: raise reject_steps";
+                throw Fail{KC_ERR_STEP_LIMIT};
+            }
+            const int64_t B = std::min<int64_t>(p.BW, ntrees - accepted);
+            if (g->next_sid + B > ((int64_t)1 << 32)) {
+                g->last_error = "kc_sample: sample ids must stay below 2^32";
+                throw Fail{KC_ERR_INVALID_ARG};
+            }
+            Carved c = carve(g, p);
+            WaveView w = c.wv;
+            w.B = B;
+            KC_CK(g, cudaMemsetAsync(g->d_err, 0, 2 * sizeof(uint32_t), g->stream));
+            KC_CK(g, cudaMemsetAsync(w.f, 0, sizeof(int64_t) * (size_t)B, g->stream));
+            KC_CK(g, launch_iota(c.sids, g->next_sid, B, g->stream));
+            {
+                Phase ph(g, g->t_init);
+                KC_CK(g, launch_wave_init(gv, w, g->stream));
+                ph.done(1);
+            }
+            {
+                Phase ph(g, g->t_wilson);
+                KC_CK(g, launch_wilson_warp_reject(gv, w, g->seed, c.sids, g->d_sorder,
+                                                   g->cfg.reject_steps, g->stream));
+                ph.done(1);
+            }
+            uint32_t hdr[2] = {0, 0};
+            KC_CK(g, copy_sync(g, hdr, g->d_err, sizeof(hdr), cudaMemcpyDeviceToHost));
+            if (hdr[0]) {
+                g->last_error = "Wilson walkers reached an inconsistent state or the iteration cap";
+                throw Fail{KC_ERR_CUDA};
+            }
+            std::vector<int64_t> st((size_t)B), f((size_t)B);
+            KC_CK(g, copy_sync(g, st.data(), w.steps, sizeof(int64_t) * (size_t)B,
+                               cudaMemcpyDeviceToHost));
+            int64_t na = 0;
+            for (int64_t t = 0; t < B; ++t)
+                if (st[(size_t)t] >= 0) g->h_map[na++] = (int32_t)t;
+            if (na > 0) {
+                KC_CK(g, cudaMemcpyAsync(g->d_map, g->h_map, sizeof(int32_t) * (size_t)na,
+                                         cudaMemcpyHostToDevice, g->stream));
+                if (p.bit) {
+                    ensure_stack(g, p, hdr[1]);
+                    c = carve(g, p);
+                }
+                for (int64_t off = 0; off < na; off += p.BT) {
+                    WaveView sv = c.wv;
+                    sv.B = std::min<int64_t>(p.BT, na - off);
+                    sv.tmap = g->d_map + off;
+                    {
+                        Phase ph(g, g->t_traverse);
+                        int nl = 0;
+                        KC_CK(g, launch_traverse(gv, sv, p.bit, g->stream, &nl, fast_traversal(g)));
+                        ph.done(nl);
+                    }
+                    {
+                        Phase ph(g, g->t_ttf);
+                        if (p.bit) KC_CK(g, launch_ttf_bit(gv, sv, g->stream));
+                        else KC_CK(g, launch_ttf_scan(gv, sv, g->stream));
+                        ph.done(1);
+                    }
+                }
+                KC_CK(g, copy_sync(g, hdr, g->d_err, sizeof(hdr), cudaMemcpyDeviceToHost));
+                if (hdr[0] & kErrBadTree) {
+                    g->last_error = "inconsistent tree state or traversal stack overflow";
+                    throw Fail{KC_ERR_CUDA};
+                }
+                KC_CK(g, copy_sync(g, f.data(), w.f, sizeof(int64_t) * (size_t)B,
+                                   cudaMemcpyDeviceToHost));
+                std::vector<int64_t> af((size_t)na), as((size_t)na), ai((size_t)na);
+                std::vector<double> aw((size_t)na, 1.0);
+                for (int64_t k = 0; k < na; ++k) {
+                    const int32_t t = g->h_map[k];
+                    af[(size_t)k] = f[(size_t)t];
+                    as[(size_t)k] = st[(size_t)t];
+                    ai[(size_t)k] = g->next_sid + t;
+                }
+                const size_t b8 = sizeof(int64_t) * (size_t)na;
+                KC_CK(g, cudaMemcpyAsync(g->d_f + g->pool, af.data(), b8, cudaMemcpyHostToDevice,
+                                         g->stream));
+                KC_CK(g, cudaMemcpyAsync(g->d_steps + g->pool, as.data(), b8,
+                                         cudaMemcpyHostToDevice, g->stream));
+                KC_CK(g, cudaMemcpyAsync(g->d_sid + g->pool, ai.data(), b8, cudaMemcpyHostToDevice,
+                                         g->stream));
+                KC_CK(g, cudaMemcpyAsync(g->d_w + g->pool, aw.data(), sizeof(double) * (size_t)na,
+                                         cudaMemcpyHostToDevice, g->stream));
+                KC_CK(g, cudaStreamSynchronize(g->stream));
+                for (int64_t k = 0; k < na; ++k) g->h_modified[(size_t)(g->pool + k)] = 0;
+                g->pool += na;
+            }
+            g->last_wave = B;
+            g->trees_rejected += B - na;
+            g->next_sid += B;
+            accepted += na;
+        }
+    } catch (Fail &) {
+        g->pool = pool0;
+        g->next_sid = sid_base;
+        throw;
+    }
+}
+
 void do_sample(kc_graph *g, int64_t ntrees) {
     if (ntrees <= 0) return;
+    if (g->cfg.reject_steps > 0) {
+        do_sample_reject(g, ntrees);
+        return;
+    }
     ensure_pool(g, g->pool + ntrees);
     Plan p = plan_for(g, ntrees, false);
     ensure_ws(g, p);
@@ -1453,6 +1573,13 @@ kc_status kc_graph_create(int64_t n, const int64_t *row_off, const int32_t *col,
         cfg.hybrid_prefix_permille < 0 || cfg.hybrid_tail_permille < 0 ||
         cfg.tau0_kind < KC_TAU0_BFS || cfg.tau0_kind > KC_TAU0_WILSON)
         return KC_ERR_INVALID_ARG;
+    // rejection by walk length: the 32-walker kernel, static pools, and a cap a
+    // tree can meet (every non-root vertex departs at least once)
+    if (cfg.reject_steps < 0 ||
+        (cfg.reject_steps > 0 &&
+         (cfg.reject_steps < n - 1 || cfg.keep_trees || cfg.autotune ||
+          (cfg.walker != KC_WALK_AUTO && cfg.walker != KC_WALK_WARP))))
+        return KC_ERR_INVALID_ARG;
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
         (void)cudaGetLastError();
@@ -1675,6 +1802,7 @@ kc_status kc_sample_multi(kc_graph *const *graphs, const uint64_t *seeds, const 
         for (int32_t j = 0; j < i; ++j)
             if (graphs[j] == g) return KC_ERR_INVALID_ARG;
         if (g->device != graphs[0]->device) return KC_ERR_INVALID_ARG;
+        if (g->cfg.reject_steps > 0) return KC_ERR_INVALID_ARG;
         if (g->seeded && seeds[i] != g->seed) {
             g->last_error = "kc_sample_multi: the handle is already seeded with a different seed";
             return KC_ERR_INVALID_ARG;
@@ -1892,6 +2020,7 @@ kc_status kc_stats(kc_graph *g, kc_stats_t *out) {
     out->tuned = g->tuned ? 1 : 0;
     for (int k = 0; k < 4; ++k) out->tune_ms[k] = g->tune_ms[k];
     out->resident_trees = g->resident_trees;
+    out->trees_rejected = g->trees_rejected;
     out->ms_wilson = g->t_wilson.ms;
     out->ms_traverse = g->t_traverse.ms;
     out->ms_ttf = g->t_ttf.ms;

@@ -237,6 +237,7 @@ struct kc_graph {
     int64_t last_wave = 0;
     int64_t total_steps = 0;
     int64_t updates_applied = 0, trees_resampled = 0;
+    int64_t trees_rejected = 0;  // abandoned by rejection by walk length
     int64_t update_seq = 0;
     double last_r = 0.0;
     int64_t last_cg_iters = 0;
@@ -338,6 +339,11 @@ cudaError_t launch_wilson_warp(const GraphView &g, WaveView w, uint64_t seed, co
                                const int32_t *sorder, int64_t step_cap, cudaStream_t s,
                                const int32_t *rs_q = nullptr, const int32_t *rs_pos = nullptr,
                                int32_t *done_flag = nullptr);
+// 32 walkers per tree with rejection by walk length: a tree whose departures
+// exceed tree_cap gets steps = -1 and no depth, order or finished words
+cudaError_t launch_wilson_warp_reject(const GraphView &g, WaveView w, uint64_t seed,
+                                      const int64_t *sids, const int32_t *sorder,
+                                      int64_t tree_cap, cudaStream_t s);
 // Traversal modes: kTravCanonical numbers children in ascending id (the DFN the
 // oracle reports and the update kernels enumerate by); the others give some
 // valid DFN (enough for f): kTravChunked (warp per tree, for deep trees and

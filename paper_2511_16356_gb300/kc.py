@@ -44,7 +44,7 @@ class kc_config(ctypes.Structure):
         ("mem_fraction", ctypes.c_double), ("sample_id_base", ctypes.c_int64),
         ("hybrid_prefix_permille", ctypes.c_int32), ("hybrid_tail_permille", ctypes.c_int32),
         ("tau0_kind", ctypes.c_int32), ("reserved1", ctypes.c_int32),
-        ("tau0_seed", ctypes.c_uint64),
+        ("tau0_seed", ctypes.c_uint64), ("reject_steps", ctypes.c_int64),
     ]
 
 
@@ -72,7 +72,8 @@ _STATS_FIELDS = [
     ("wf_sum", ctypes.c_double), ("w_sum", ctypes.c_double), ("x2_sum", ctypes.c_double),
     ("last_resistance", ctypes.c_double), ("last_cg_iters", ctypes.c_int64),
     ("traversal", ctypes.c_int32), ("tuned", ctypes.c_int32),
-    ("tune_ms", ctypes.c_double * 4), ("resident_trees", ctypes.c_int64),
+    ("tune_ms", ctypes.c_double * 4), ("trees_rejected", ctypes.c_int64),
+    ("resident_trees", ctypes.c_int64),
 ]
 
 

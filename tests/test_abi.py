@@ -87,6 +87,37 @@ def test_no_device_is_reported(lib):
     assert np.all(g.deg == 2)
 
 
+def test_rejection_config_is_checked_before_any_device_work(lib):
+    """Rejection by walk length needs the 32-walker kernel, static pools, no
+    autotune and a cap of at least n - 1 departures (each non-root vertex
+    departs once): anything else is INVALID_ARG before the device is touched;
+    a valid setting passes on to the device check."""
+    from paper_2511_16356_gb300 import kc
+    from paper_2511_16356_gb300 import synth as S
+
+    g = S.cycle(12)
+
+    def status(**kw):
+        c = kc.kc_config_default()
+        c.keep_trees = 0
+        for k, v in kw.items():
+            setattr(c, k, v)
+        st, h = kc.kc_graph_create(g.row_off, g.col, c, check=False)
+        if h:
+            kc.kc_graph_destroy(h)
+        return kc.STATUS[st]
+
+    assert kc.kc_config_default().reject_steps == 0
+    assert status(reject_steps=-1) == "KC_ERR_INVALID_ARG"
+    assert status(reject_steps=10) == "KC_ERR_INVALID_ARG"            # below n - 1 = 11
+    assert status(reject_steps=100, keep_trees=1) == "KC_ERR_INVALID_ARG"
+    assert status(reject_steps=100, autotune=1) == "KC_ERR_INVALID_ARG"
+    assert status(reject_steps=100, walker=kc.KC_WALK_LANE) == "KC_ERR_INVALID_ARG"
+    assert status(reject_steps=100, walker=kc.KC_WALK_HYBRID) == "KC_ERR_INVALID_ARG"
+    if not os.path.exists("/dev/nvidia0"):
+        assert status(reject_steps=11) == "KC_ERR_NO_DEVICE"
+
+
 def test_server_config_defaults(lib):
     import ctypes
 
