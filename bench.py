@@ -496,6 +496,11 @@ def main():
                     help="trees per graph in the batched multi-graph leg")
     ap.add_argument("--serve-load", type=float, default=1.5,
                     help="offered query rate as a multiple of the plain path's capacity")
+    ap.add_argument("--reject-quantile", type=float, default=0.0,
+                    help="rejection by walk length with the cap at this quantile of a probe "
+                         "batch's step counts (0: off)")
+    ap.add_argument("--reject-probe", type=int, default=256,
+                    help="trees of the probe batch that sets the rejection cap")
     ap.add_argument("--dynamic", action="store_true",
                     help="also run the update-stream leg (ISM against BSM)")
     ap.add_argument("--dyn-n", type=int, default=100000)
@@ -532,6 +537,17 @@ def main():
                   "lane": kc.KC_WALK_LANE, "hybrid": kc.KC_WALK_HYBRID}[args.walker]
     cfg.hybrid_prefix_permille = args.hybrid_prefix
     cfg.hybrid_tail_permille = args.hybrid_tail
+    reject = None
+    if args.reject_quantile > 0:
+        # rejection by walk length: the cap is a quantile of the step counts of
+        # a probe batch (a rule on step counts only, so the trees stay uniform)
+        P = kc.KemenyGraph.from_graph(g, cfg, stream=stream.cuda_stream)
+        P.sample(args.seed, args.reject_probe)
+        probe_steps = P.samples()["steps"]
+        P.close()
+        cfg.reject_steps = max(int(np.quantile(probe_steps, args.reject_quantile)), n - 1)
+        reject = {"quantile": args.reject_quantile, "probe_trees": args.reject_probe,
+                  "reject_steps": int(cfg.reject_steps)}
     G = kc.KemenyGraph.from_graph(g, cfg, stream=stream.cuda_stream)
     st0 = G.stats()
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.int32, device="cuda")
@@ -543,6 +559,7 @@ def main():
     torch.cuda.synchronize()
     kc.kc_reset_timers(G.h)
     pool0 = G.stats()["pool_trees"]
+    rej0 = G.stats()["trees_rejected"]
     clocks = ClockSampler(local)
     barrier(dist)
     torch.cuda.synchronize()
@@ -621,6 +638,9 @@ def main():
                                              trees_timed, steps_total)
                                   / (tot_ms / 1000.0) / 1e9 / peak},
         "phase_ms": phase_ms,
+        "rejection": None if reject is None else
+        dict(reject, trees_rejected=int(st["trees_rejected"] - rej0),
+             note="trees/s counts accepted trees; the roofline counts their steps only"),
         "steps_per_tree": steps_total / trees_timed,
         "gpu_launches": int(launches),
         "clocks": clk,
