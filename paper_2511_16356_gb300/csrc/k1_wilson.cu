@@ -513,7 +513,13 @@ __global__ void __launch_bounds__(kWarpWalkerBlock, 24)
     }
     if constexpr (kReject) {
         if (rejected) {
-            if (lane == 0) w.steps[t] = -1;
+            if (lane == 0) {
+                w.steps[t] = -1;
+                if (done_flag) {
+                    __threadfence_system();
+                    done_flag[t] = -1;  // finished, rejected
+                }
+            }
             return;
         }
     }
@@ -523,13 +529,21 @@ __global__ void __launch_bounds__(kWarpWalkerBlock, 24)
     int md = maxd;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) md = max(md, __shfl_down_sync(kFull, md, o));
+    const bool over = kReject && __shfl_sync(kFull, tot, 0) > step_cap;
     if (lane == 0) {
-        if (kReject && tot > step_cap) {
+        if (over) {
             w.steps[t] = -1;  // finished between two checks, but past the cap
         } else {
             w.steps[t] = (rs_q ? w.steps[t] : 0) + tot;
             atomicMax(w.maxdepth, md);
         }
+    }
+    if (done_flag && over) {
+        if (lane == 0) {
+            __threadfence_system();
+            done_flag[t] = -1;  // finished, rejected
+        }
+        return;
     }
     if (done_flag) {
         // publish the finished tree (its depth + 1) to the host, after every
@@ -558,12 +572,12 @@ cudaError_t launch_wilson_warp(const GraphView &g, WaveView w, uint64_t seed, co
 
 cudaError_t launch_wilson_warp_reject(const GraphView &g, WaveView w, uint64_t seed,
                                       const int64_t *sids, const int32_t *sorder,
-                                      int64_t tree_cap, cudaStream_t s) {
+                                      int64_t tree_cap, cudaStream_t s, int32_t *done_flag) {
     // tree_cap bounds the whole tree's departures, and an iteration may move
     // as little as one lane: a generous bound that no accepted tree reaches
     const int64_t iter_cap = 16 * std::min<int64_t>(tree_cap, (int64_t)1 << 40) + 64 * g.n + 4096;
     k_wilson_warp<false, true><<<(unsigned)w.B, kWarpWalkerBlock, 0, s>>>(
-        g, w, seed, sids, sorder, tree_cap, iter_cap, nullptr, nullptr, nullptr, MultiWalk{});
+        g, w, seed, sids, sorder, tree_cap, iter_cap, nullptr, nullptr, done_flag, MultiWalk{});
     return cudaGetLastError();
 }
 

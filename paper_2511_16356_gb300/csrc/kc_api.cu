@@ -298,7 +298,9 @@ void ensure_pipeline(kc_graph *g, int64_t B) {
 // memory, the host gathers finished trees into chunks of up to BT (a tree map
 // per chunk) and launches their sub-wave kernels; only the chunk holding the
 // slowest trees waits for the end of the walk.
-void run_wave_pipelined(kc_graph *g, Plan &p, int64_t B, int64_t sid0) {
+// With reject, the walk abandons trees past cfg.reject_steps departures; they
+// flag -1 and are left out of the chunks (their f stays 0, their steps -1).
+void run_wave_pipelined(kc_graph *g, Plan &p, int64_t B, int64_t sid0, bool reject = false) {
     ensure_pipeline(g, B);
     GraphView gv = view_of(g);
     Carved c = carve(g, p);
@@ -332,16 +334,20 @@ void run_wave_pipelined(kc_graph *g, Plan &p, int64_t B, int64_t sid0) {
     KC_CK(g, cudaEventRecord(ev_ready, s1));
     KC_CK(g, cudaStreamWaitEvent(s2, ev_ready, 0));
     KC_CK(g, cudaEventRecord(ev_w0, s1));
-    KC_CK(g, launch_wilson_warp(gv, w, g->seed, c.sids, g->d_sorder, step_cap_of(g), s1, nullptr,
-                                nullptr, g->d_done));
+    if (reject)
+        KC_CK(g, launch_wilson_warp_reject(gv, w, g->seed, c.sids, g->d_sorder,
+                                           g->cfg.reject_steps, s1, g->d_done));
+    else
+        KC_CK(g, launch_wilson_warp(gv, w, g->seed, c.sids, g->d_sorder, step_cap_of(g), s1,
+                                    nullptr, nullptr, g->d_done));
     KC_CK(g, cudaEventRecord(ev_w1, s1));
     const int64_t chunk_min = std::max<int64_t>(1, std::min<int64_t>(p.BT, (B + 1) / 2));
     std::vector<int32_t> unseen((size_t)B), ready;
     for (int64_t t = 0; t < B; ++t) unseen[(size_t)t] = (int32_t)t;
     std::vector<std::array<cudaEvent_t, 3>> chunk_ev;
-    int64_t processed = 0;
+    int64_t processed = 0, skipped = 0;  // trees put into chunks / rejected
     bool wdone = false;
-    while (processed < B) {
+    while (processed + skipped < B) {
         if (!wdone) {
             const cudaError_t q = cudaEventQuery(ev_w1);
             if (q == cudaSuccess) wdone = true;
@@ -350,7 +356,9 @@ void run_wave_pipelined(kc_graph *g, Plan &p, int64_t B, int64_t sid0) {
         size_t keep = 0;
         for (size_t i = 0; i < unseen.size(); ++i) {
             const int32_t t = unseen[i];
-            if (hd[t] != 0) ready.push_back(t);
+            const int32_t flag = hd[t];
+            if (flag > 0) ready.push_back(t);
+            else if (flag < 0) ++skipped;
             else unseen[keep++] = t;
         }
         unseen.resize(keep);
@@ -1100,17 +1108,82 @@ void autotune(kc_graph *g, Plan &p, int64_t B, int64_t sid0) {
     g->tuned = true;
 }
 
+// Rejection by walk length, one wave of B trees from sample id sid0 without
+// pipelining: the walk, then the accepted trees' traversal and f through a
+// tree map.  Leaves steps (-1: rejected) and f in the carved workspace.
+void run_wave_reject(kc_graph *g, Plan &p, int64_t B, int64_t sid0) {
+    const GraphView gv = view_of(g);
+    Carved c = carve(g, p);
+    WaveView w = c.wv;
+    w.B = B;
+    KC_CK(g, cudaMemsetAsync(g->d_err, 0, 2 * sizeof(uint32_t), g->stream));
+    KC_CK(g, cudaMemsetAsync(w.f, 0, sizeof(int64_t) * (size_t)B, g->stream));
+    KC_CK(g, launch_iota(c.sids, sid0, B, g->stream));
+    {
+        Phase ph(g, g->t_init);
+        KC_CK(g, launch_wave_init(gv, w, g->stream));
+        ph.done(1);
+    }
+    {
+        Phase ph(g, g->t_wilson);
+        KC_CK(g, launch_wilson_warp_reject(gv, w, g->seed, c.sids, g->d_sorder,
+                                           g->cfg.reject_steps, g->stream));
+        ph.done(1);
+    }
+    uint32_t hdr[2] = {0, 0};
+    KC_CK(g, copy_sync(g, hdr, g->d_err, sizeof(hdr), cudaMemcpyDeviceToHost));
+    if (hdr[0]) {
+        g->last_error = "Wilson walkers reached an inconsistent state or the iteration cap";
+        throw Fail{KC_ERR_CUDA};
+    }
+    std::vector<int64_t> st((size_t)B);
+    KC_CK(g, copy_sync(g, st.data(), w.steps, sizeof(int64_t) * (size_t)B,
+                       cudaMemcpyDeviceToHost));
+    int64_t na = 0;
+    for (int64_t t = 0; t < B; ++t)
+        if (st[(size_t)t] >= 0) g->h_map[na++] = (int32_t)t;
+    if (na == 0) return;
+    KC_CK(g, cudaMemcpyAsync(g->d_map, g->h_map, sizeof(int32_t) * (size_t)na,
+                             cudaMemcpyHostToDevice, g->stream));
+    if (p.bit) {
+        ensure_stack(g, p, hdr[1]);
+        c = carve(g, p);
+    }
+    for (int64_t off = 0; off < na; off += p.BT) {
+        WaveView sv = c.wv;
+        sv.B = std::min<int64_t>(p.BT, na - off);
+        sv.tmap = g->d_map + off;
+        {
+            Phase ph(g, g->t_traverse);
+            int nl = 0;
+            KC_CK(g, launch_traverse(gv, sv, p.bit, g->stream, &nl, fast_traversal(g)));
+            ph.done(nl);
+        }
+        {
+            Phase ph(g, g->t_ttf);
+            if (p.bit) KC_CK(g, launch_ttf_bit(gv, sv, g->stream));
+            else KC_CK(g, launch_ttf_scan(gv, sv, g->stream));
+            ph.done(1);
+        }
+    }
+    KC_CK(g, copy_sync(g, hdr, g->d_err, sizeof(hdr), cudaMemcpyDeviceToHost));
+    if (hdr[0] & kErrBadTree) {
+        g->last_error = "inconsistent tree state or traversal stack overflow";
+        throw Fail{KC_ERR_CUDA};
+    }
+}
+
 // Rejection by walk length: waves of the 32-walker kernel abandon trees past
 // cfg.reject_steps departures; each wave's accepted trees are traversed and
-// evaluated through a tree map and appended to the pool in sample-id order,
-// until ntrees are accepted.  Rejected ids are consumed (never reused).
+// evaluated (overlapping the walk, as pipelined waves do, on large graphs) and
+// appended to the pool in sample-id order, until ntrees are accepted.
+// Rejected ids are consumed (never reused).
 void do_sample_reject(kc_graph *g, int64_t ntrees) {
     ensure_pool(g, g->pool + ntrees);
     Plan p = plan_for(g, ntrees, false);
     ensure_ws(g, p);
-    ensure_pipeline(g, p.BW);  // tree-map staging: h_map / d_map
+    ensure_pipeline(g, p.BW);  // done flags and tree-map staging
     const int64_t pool0 = g->pool, sid_base = g->next_sid;
-    const GraphView gv = view_of(g);
     try {
         int64_t accepted = 0;
         while (accepted < ntrees) {
@@ -1123,74 +1196,24 @@ void do_sample_reject(kc_graph *g, int64_t ntrees) {
                 g->last_error = "kc_sample: sample ids must stay below 2^32";
                 throw Fail{KC_ERR_INVALID_ARG};
             }
-            Carved c = carve(g, p);
-            WaveView w = c.wv;
-            w.B = B;
-            KC_CK(g, cudaMemsetAsync(g->d_err, 0, 2 * sizeof(uint32_t), g->stream));
-            KC_CK(g, cudaMemsetAsync(w.f, 0, sizeof(int64_t) * (size_t)B, g->stream));
-            KC_CK(g, launch_iota(c.sids, g->next_sid, B, g->stream));
-            {
-                Phase ph(g, g->t_init);
-                KC_CK(g, launch_wave_init(gv, w, g->stream));
-                ph.done(1);
-            }
-            {
-                Phase ph(g, g->t_wilson);
-                KC_CK(g, launch_wilson_warp_reject(gv, w, g->seed, c.sids, g->d_sorder,
-                                                   g->cfg.reject_steps, g->stream));
-                ph.done(1);
-            }
-            uint32_t hdr[2] = {0, 0};
-            KC_CK(g, copy_sync(g, hdr, g->d_err, sizeof(hdr), cudaMemcpyDeviceToHost));
-            if (hdr[0]) {
-                g->last_error = "Wilson walkers reached an inconsistent state or the iteration cap";
-                throw Fail{KC_ERR_CUDA};
-            }
+            if (B > 1 && (B > p.BT || g->n >= (1 << 16))) run_wave_pipelined(g, p, B, g->next_sid, true);
+            else run_wave_reject(g, p, B, g->next_sid);
+            const WaveView w = carve(g, p).wv;
             std::vector<int64_t> st((size_t)B), f((size_t)B);
             KC_CK(g, copy_sync(g, st.data(), w.steps, sizeof(int64_t) * (size_t)B,
                                cudaMemcpyDeviceToHost));
-            int64_t na = 0;
-            for (int64_t t = 0; t < B; ++t)
-                if (st[(size_t)t] >= 0) g->h_map[na++] = (int32_t)t;
+            KC_CK(g, copy_sync(g, f.data(), w.f, sizeof(int64_t) * (size_t)B,
+                               cudaMemcpyDeviceToHost));
+            std::vector<int64_t> af, as, ai;
+            for (int64_t t = 0; t < B; ++t) {
+                if (st[(size_t)t] < 0) continue;
+                af.push_back(f[(size_t)t]);
+                as.push_back(st[(size_t)t]);
+                ai.push_back(g->next_sid + t);
+            }
+            const int64_t na = (int64_t)af.size();
             if (na > 0) {
-                KC_CK(g, cudaMemcpyAsync(g->d_map, g->h_map, sizeof(int32_t) * (size_t)na,
-                                         cudaMemcpyHostToDevice, g->stream));
-                if (p.bit) {
-                    ensure_stack(g, p, hdr[1]);
-                    c = carve(g, p);
-                }
-                for (int64_t off = 0; off < na; off += p.BT) {
-                    WaveView sv = c.wv;
-                    sv.B = std::min<int64_t>(p.BT, na - off);
-                    sv.tmap = g->d_map + off;
-                    {
-                        Phase ph(g, g->t_traverse);
-                        int nl = 0;
-                        KC_CK(g, launch_traverse(gv, sv, p.bit, g->stream, &nl, fast_traversal(g)));
-                        ph.done(nl);
-                    }
-                    {
-                        Phase ph(g, g->t_ttf);
-                        if (p.bit) KC_CK(g, launch_ttf_bit(gv, sv, g->stream));
-                        else KC_CK(g, launch_ttf_scan(gv, sv, g->stream));
-                        ph.done(1);
-                    }
-                }
-                KC_CK(g, copy_sync(g, hdr, g->d_err, sizeof(hdr), cudaMemcpyDeviceToHost));
-                if (hdr[0] & kErrBadTree) {
-                    g->last_error = "inconsistent tree state or traversal stack overflow";
-                    throw Fail{KC_ERR_CUDA};
-                }
-                KC_CK(g, copy_sync(g, f.data(), w.f, sizeof(int64_t) * (size_t)B,
-                                   cudaMemcpyDeviceToHost));
-                std::vector<int64_t> af((size_t)na), as((size_t)na), ai((size_t)na);
                 std::vector<double> aw((size_t)na, 1.0);
-                for (int64_t k = 0; k < na; ++k) {
-                    const int32_t t = g->h_map[k];
-                    af[(size_t)k] = f[(size_t)t];
-                    as[(size_t)k] = st[(size_t)t];
-                    ai[(size_t)k] = g->next_sid + t;
-                }
                 const size_t b8 = sizeof(int64_t) * (size_t)na;
                 KC_CK(g, cudaMemcpyAsync(g->d_f + g->pool, af.data(), b8, cudaMemcpyHostToDevice,
                                          g->stream));

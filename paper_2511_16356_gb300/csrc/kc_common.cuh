@@ -340,10 +340,12 @@ cudaError_t launch_wilson_warp(const GraphView &g, WaveView w, uint64_t seed, co
                                const int32_t *rs_q = nullptr, const int32_t *rs_pos = nullptr,
                                int32_t *done_flag = nullptr);
 // 32 walkers per tree with rejection by walk length: a tree whose departures
-// exceed tree_cap gets steps = -1 and no depth, order or finished words
+// exceed tree_cap gets steps = -1 (and done flag -1) and no depth, order or
+// finished words
 cudaError_t launch_wilson_warp_reject(const GraphView &g, WaveView w, uint64_t seed,
                                       const int64_t *sids, const int32_t *sorder,
-                                      int64_t tree_cap, cudaStream_t s);
+                                      int64_t tree_cap, cudaStream_t s,
+                                      int32_t *done_flag = nullptr);
 // Traversal modes: kTravCanonical numbers children in ascending id (the DFN the
 // oracle reports and the update kernels enumerate by); the others give some
 // valid DFN (enough for f): kTravChunked (warp per tree, for deep trees and
