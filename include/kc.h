@@ -337,6 +337,39 @@ kc_status kc_stats(kc_graph *g, kc_stats_t *out);
 kc_status kc_reset_timers(kc_graph *g);
 
 /*
+ * Pool sums of one handle or of several sample-id shards (the exchange step of
+ * a sample-sharded multi-GPU run; no counterpart in the paper, which samples
+ * on one machine).  f_sum is the exact int128 sum of the unit-weight f(tau) as
+ * (signed high, unsigned low) 64-bit limbs, as in kc_stats_t.
+ */
+typedef struct {
+    int64_t f_sum_hi;
+    uint64_t f_sum_lo;
+    double wf_sum;      /* sum w f / 2m  */
+    double w_sum;       /* sum w         */
+    double x2_sum;      /* sum (f / 2m)^2 */
+    int64_t count;      /* trees         */
+} kc_pool_sums;
+
+/*
+ * Combine per-shard sums (host only, no device work): the int128 f sums are
+ * added exactly; the FP64 sums are added in array order, so every rank that
+ * combines the same gathered array gets the same bits.  Errors: INVALID_ARG
+ * (NULL pointers, count < 1, or an int128 overflow of f_sum).
+ */
+kc_status kc_combine_sums(const kc_pool_sums *parts, int32_t count, kc_pool_sums *out);
+
+/*
+ * K_hat from (combined) pool sums (host only): with unit_weights the exact
+ * numerator over 2m omega, K_hat = f_sum / (2m count) (Theorem 3, Algorithm 1's
+ * last line: one FP64 division of the int128 sum, as kc_estimate does);
+ * otherwise the weighted mean sum w f / (2m sum w) (Algorithm 3).
+ * Errors: INVALID_ARG (NULL, twom < 2, count < 1, or w_sum <= 0 when weighted).
+ */
+kc_status kc_estimate_from_sums(const kc_pool_sums *sums, int64_t twom, int32_t unit_weights,
+                                double *K_out);
+
+/*
  * Wilson sampling without any device allocation.  (The paper has no
  * counterpart: this is an interface for callers that cannot allocate.)
  *
@@ -356,7 +389,8 @@ kc_status kc_reset_timers(kc_graph *g);
  *  step_cap          per-tree cap on departures (0: max(2^22, 1024 n))
  *  d_parent          device int32[n_trees][n] out: parent of each vertex (-1 at root)
  *  d_steps           device int64[n_trees] out: Wilson departures per tree
- *  d_status          device uint32[1] out: 0, or 1 if a tree hit step_cap
+ *  d_status          device uint32[1] out: 0, or 1 if a tree hit step_cap or one
+ *                    vertex departed 2^25 times (the other samplers' limit)
  *  stream            cudaStream_t to run on (NULL: legacy default stream)
  * Work is enqueued on `stream`; the call returns without synchronising.
  * Requires n * n_trees <= 8 Mi, else KC_ERR_SCRATCH_LIMIT.  The first call on

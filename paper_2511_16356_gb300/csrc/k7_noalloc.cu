@@ -61,7 +61,10 @@ k_wilson_noalloc(int64_t n, const int64_t *__restrict__ row_off, const int32_t *
             const uint32_t k = bounded_draw(seed, (uint32_t)u, w_count(wu), sample, kTagWalk, d);
             const int32_t v = col[off + k];
             word[u] = w_make(v, w_count(wu) + 1, false);
-            if (++steps > step_cap) {
+            // the library's samplers stop at 2^25 departures of one vertex (the
+            // 32-walker word packs the count in 25 bits); stopping here too keeps
+            // the contract identical and the 31-bit field from wrapping
+            if (++steps > step_cap || w_count(wu) + 1 >= (1u << 25)) {
                 ok = false;
                 break;
             }
@@ -89,9 +92,11 @@ extern "C" kc_status kc_wilson_noalloc(int64_t n, const int64_t *d_row_off, cons
                                        int64_t n_trees, int64_t step_cap, int32_t *d_parent,
                                        int64_t *d_steps, uint32_t *d_status, void *stream) {
     using namespace kc;
+    // sample ids are 32-bit: first_sample_id + n_trees <= 2^32, checked without
+    // forming the sum of two unchecked values
     if (n < 2 || n_trees < 0 || !d_row_off || !d_col || !d_parent || !d_steps || !d_status ||
-        root < 0 || root >= n || first_sample_id < 0 ||
-        first_sample_id + n_trees > ((int64_t)1 << 32))
+        root < 0 || root >= n || first_sample_id < 0 || first_sample_id > ((int64_t)1 << 32) ||
+        n_trees > ((int64_t)1 << 32) - first_sample_id)
         return KC_ERR_INVALID_ARG;
     if (n_trees == 0) return KC_OK;
     if (n > kNoAllocWords / n_trees) return KC_ERR_SCRATCH_LIMIT;

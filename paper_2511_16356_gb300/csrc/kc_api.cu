@@ -1132,6 +1132,11 @@ void run_wave_reject(kc_graph *g, Plan &p, int64_t B, int64_t sid0) {
     }
     uint32_t hdr[2] = {0, 0};
     KC_CK(g, copy_sync(g, hdr, g->d_err, sizeof(hdr), cudaMemcpyDeviceToHost));
+    if (hdr[0] & kErrStepLimit) {
+        // a single vertex's departure counter filled its 25 bits
+        g->last_error = "Wilson walk exceeded the per-vertex departure limit";
+        throw Fail{KC_ERR_STEP_LIMIT};
+    }
     if (hdr[0]) {
         g->last_error = "Wilson walkers reached an inconsistent state or the iteration cap";
         throw Fail{KC_ERR_CUDA};
@@ -1177,13 +1182,28 @@ void run_wave_reject(kc_graph *g, Plan &p, int64_t B, int64_t sid0) {
 // cfg.reject_steps departures; each wave's accepted trees are traversed and
 // evaluated (overlapping the walk, as pipelined waves do, on large graphs) and
 // appended to the pool in sample-id order, until ntrees are accepted.
-// Rejected ids are consumed (never reused).
+// A wave draws about need / rate trees, rate being the acceptance rate seen on
+// this handle so far (1/8 more than needed before any is seen), so that one
+// wave usually suffices; of its accepted trees only the first `need` in id
+// order are kept, and the ids after the last kept one are left for the next
+// call.  Rejected ids below it are consumed (never reused).
 void do_sample_reject(kc_graph *g, int64_t ntrees) {
+    auto wave_size = [&](int64_t need) {
+        const double rate = g->rej_drawn > 0
+                                ? std::max(1.0 / 64.0, (double)(g->rej_accepted + 1) /
+                                                           (double)(g->rej_drawn + 1))
+                                : 8.0 / 9.0;
+        // expected draws plus three standard deviations of the accepted count
+        const double want = (double)need / rate;
+        const double sd = std::sqrt(want * rate * (1.0 - rate)) / rate;
+        return (int64_t)std::ceil(want + 3.0 * sd) + 8;
+    };
     ensure_pool(g, g->pool + ntrees);
-    Plan p = plan_for(g, ntrees, false);
+    Plan p = plan_for(g, wave_size(ntrees), false);
     ensure_ws(g, p);
     ensure_pipeline(g, p.BW);  // done flags and tree-map staging
-    const int64_t pool0 = g->pool, sid_base = g->next_sid;
+    const int64_t pool0 = g->pool, sid_base = g->next_sid, rej0 = g->trees_rejected;
+    const int64_t drawn0 = g->rej_drawn, acc0 = g->rej_accepted;
     try {
         int64_t accepted = 0;
         while (accepted < ntrees) {
@@ -1191,13 +1211,25 @@ void do_sample_reject(kc_graph *g, int64_t ntrees) {
                 g->last_error = "rejection by walk length accepts too few trees: raise reject_steps";
                 throw Fail{KC_ERR_STEP_LIMIT};
             }
-            const int64_t B = std::min<int64_t>(p.BW, ntrees - accepted);
-            if (g->next_sid + B > ((int64_t)1 << 32)) {
+            const int64_t need = ntrees - accepted;
+            int64_t B = std::min<int64_t>(p.BW, wave_size(need));
+            B = std::min<int64_t>(B, ((int64_t)1 << 32) - g->next_sid);
+            if (B <= 0) {
                 g->last_error = "kc_sample: sample ids must stay below 2^32";
                 throw Fail{KC_ERR_INVALID_ARG};
             }
-            if (B > 1 && (B > p.BT || g->n >= (1 << 16))) run_wave_pipelined(g, p, B, g->next_sid, true);
-            else run_wave_reject(g, p, B, g->next_sid);
+            if (B > 1 && (B > p.BT || g->n >= (1 << 16))) {
+                try {
+                    run_wave_pipelined(g, p, B, g->next_sid, true);
+                } catch (Fail &) {
+                    // let both streams drain before the workspace is reused
+                    cudaStreamSynchronize(g->stream);
+                    if (g->stream2) cudaStreamSynchronize(g->stream2);
+                    throw;
+                }
+            } else {
+                run_wave_reject(g, p, B, g->next_sid);
+            }
             const WaveView w = carve(g, p).wv;
             std::vector<int64_t> st((size_t)B), f((size_t)B);
             KC_CK(g, copy_sync(g, st.data(), w.steps, sizeof(int64_t) * (size_t)B,
@@ -1205,11 +1237,15 @@ void do_sample_reject(kc_graph *g, int64_t ntrees) {
             KC_CK(g, copy_sync(g, f.data(), w.f, sizeof(int64_t) * (size_t)B,
                                cudaMemcpyDeviceToHost));
             std::vector<int64_t> af, as, ai;
+            int64_t used = B, wave_acc = 0;  // ids consumed; accepted in the whole wave
             for (int64_t t = 0; t < B; ++t) {
                 if (st[(size_t)t] < 0) continue;
+                ++wave_acc;
+                if ((int64_t)af.size() == need) continue;
                 af.push_back(f[(size_t)t]);
                 as.push_back(st[(size_t)t]);
                 ai.push_back(g->next_sid + t);
+                if ((int64_t)af.size() == need) used = t + 1;
             }
             const int64_t na = (int64_t)af.size();
             if (na > 0) {
@@ -1228,13 +1264,18 @@ void do_sample_reject(kc_graph *g, int64_t ntrees) {
                 g->pool += na;
             }
             g->last_wave = B;
-            g->trees_rejected += B - na;
-            g->next_sid += B;
+            g->trees_rejected += used - na;
+            g->next_sid += used;
+            g->rej_drawn += B;
+            g->rej_accepted += wave_acc;
             accepted += na;
         }
     } catch (Fail &) {
         g->pool = pool0;
         g->next_sid = sid_base;
+        g->trees_rejected = rej0;
+        g->rej_drawn = drawn0;
+        g->rej_accepted = acc0;
         throw;
     }
 }
@@ -2078,6 +2119,38 @@ kc_status kc_stats(kc_graph *g, kc_stats_t *out) {
             return e.st;
         }
     }
+    return KC_OK;
+}
+
+kc_status kc_combine_sums(const kc_pool_sums *parts, int32_t count, kc_pool_sums *out) {
+    if (!parts || !out || count < 1) return KC_ERR_INVALID_ARG;
+    __int128 f = 0;
+    kc_pool_sums r{};
+    for (int32_t i = 0; i < count; ++i) {
+        const kc_pool_sums &p = parts[i];
+        const __int128 v = ((__int128)p.f_sum_hi << 64) | (__int128)p.f_sum_lo;
+        if (__builtin_add_overflow(f, v, &f)) return KC_ERR_INVALID_ARG;
+        r.wf_sum += p.wf_sum;
+        r.w_sum += p.w_sum;
+        r.x2_sum += p.x2_sum;
+        if (p.count < 0 || __builtin_add_overflow(r.count, p.count, &r.count))
+            return KC_ERR_INVALID_ARG;
+    }
+    r.f_sum_hi = (int64_t)(f >> 64);
+    r.f_sum_lo = (uint64_t)f;
+    *out = r;
+    return KC_OK;
+}
+
+kc_status kc_estimate_from_sums(const kc_pool_sums *s, int64_t twom, int32_t unit_weights,
+                                double *K_out) {
+    if (!s || !K_out || twom < 2 || s->count < 1) return KC_ERR_INVALID_ARG;
+    if (unit_weights) {
+        *K_out = i128_to_double(s->f_sum_hi, s->f_sum_lo) / ((double)twom * (double)s->count);
+        return KC_OK;
+    }
+    if (!(s->w_sum > 0)) return KC_ERR_INVALID_ARG;
+    *K_out = s->wf_sum / s->w_sum;
     return KC_OK;
 }
 

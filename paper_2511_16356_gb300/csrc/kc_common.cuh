@@ -238,6 +238,7 @@ struct kc_graph {
     int64_t total_steps = 0;
     int64_t updates_applied = 0, trees_resampled = 0;
     int64_t trees_rejected = 0;  // abandoned by rejection by walk length
+    int64_t rej_drawn = 0, rej_accepted = 0;  // trees walked / accepted under rejection
     int64_t update_seq = 0;
     double last_r = 0.0;
     int64_t last_cg_iters = 0;

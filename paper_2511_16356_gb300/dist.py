@@ -18,53 +18,76 @@ def rank_sample_base(rank: int, world: int, ids_per_rank: int = IDS_PER_RANK) ->
 
 
 def pool_sums(stats: dict) -> dict:
-    """The per-rank sums kc_stats reports, as Python numbers."""
-    hi, lo = int(stats["f_sum_hi"]), int(stats["f_sum_lo"])
-    return {"f_sum": hi * (1 << 64) + (lo & ((1 << 64) - 1)), "wf": float(stats["wf_sum"]),
-            "w": float(stats["w_sum"]), "x2": float(stats["x2_sum"]),
-            "count": int(stats["pool_trees"])}
+    """The per-rank sums kc_stats reports (the fields of kc_pool_sums)."""
+    return {k: stats[k] for k in ("f_sum_hi", "f_sum_lo", "wf_sum", "w_sum", "x2_sum")} | \
+        {"count": int(stats["pool_trees"])}
+
+
+def _as_struct(d: dict):
+    from . import kc
+
+    return kc.kc_pool_sums(int(d["f_sum_hi"]), int(d["f_sum_lo"]) & ((1 << 64) - 1),
+                           float(d["wf_sum"]), float(d["w_sum"]), float(d["x2_sum"]),
+                           int(d["count"]))
+
+
+def _as_dict(s) -> dict:
+    return {k: getattr(s, k) for k, _ in s._fields_}
 
 
 def combine_pool_sums(local: dict, group=None) -> dict:
-    """Exact cross-rank combination: the int128 f sums are gathered as limbs and
-    added as Python integers; the FP64 sums are gathered and added in rank
-    order, so every rank gets the same bits."""
+    """Every rank's kc_pool_sums gathered (the int128 f sum travels as its two
+    64-bit limbs, the FP64 sums bit for bit) and combined by kc_combine_sums,
+    which adds f exactly and the FP64 sums in rank order, so every rank gets the
+    same bits.  Without an initialised process group: this rank's sums."""
+    import ctypes
+
     import torch
     import torch.distributed as dist
 
+    from . import kc
+
     if not dist.is_available() or not dist.is_initialized():
-        return dict(local)
-    world = dist.get_world_size(group)
-    f = int(local["f_sum"])
-    limbs = [(f >> (32 * k)) & 0xFFFFFFFF for k in range(4)]  # two's complement, 128 bits
-    t = torch.tensor(limbs + [local["count"]], dtype=torch.int64)
-    ft = torch.tensor([local["wf"], local["w"], local["x2"]], dtype=torch.float64)
-    dev = "cuda" if dist.get_backend(group) == "nccl" else "cpu"
-    t, ft = t.to(dev), ft.to(dev)
-    gi = [torch.empty_like(t) for _ in range(world)]
-    gf = [torch.empty_like(ft) for _ in range(world)]
-    dist.all_gather(gi, t, group=group)
-    dist.all_gather(gf, ft, group=group)
-    out = {"f_sum": 0, "wf": 0.0, "w": 0.0, "x2": 0.0, "count": 0}
-    for a, b in zip(gi, gf):
-        a = [int(x) for x in a.cpu().tolist()]
-        v = sum(a[k] << (32 * k) for k in range(4))
-        if v >= 1 << 127:
-            v -= 1 << 128
-        out["f_sum"] += v
-        out["count"] += a[4]
-        bf = b.cpu().tolist()
-        out["wf"] += bf[0]
-        out["w"] += bf[1]
-        out["x2"] += bf[2]
-    return out
+        parts = [_as_struct(local)]
+    else:
+        world = dist.get_world_size(group)
+        ls = _as_struct(local)
+        lo_signed = ls.f_sum_lo - (1 << 64) if ls.f_sum_lo >= (1 << 63) else ls.f_sum_lo
+        t = torch.tensor([ls.f_sum_hi, lo_signed, ls.count], dtype=torch.int64)
+        ft = torch.tensor([ls.wf_sum, ls.w_sum, ls.x2_sum], dtype=torch.float64)
+        dev = "cuda" if dist.get_backend(group) == "nccl" else "cpu"
+        t, ft = t.to(dev), ft.to(dev)
+        gi = [torch.empty_like(t) for _ in range(world)]
+        gf = [torch.empty_like(ft) for _ in range(world)]
+        dist.all_gather(gi, t, group=group)
+        dist.all_gather(gf, ft, group=group)
+        parts = []
+        for a, b in zip(gi, gf):
+            hi, lo, cnt = (int(x) for x in a.cpu().tolist())
+            wf, w, x2 = b.cpu().tolist()
+            parts.append(kc.kc_pool_sums(hi, lo & ((1 << 64) - 1), wf, w, x2, cnt))
+    arr = (kc.kc_pool_sums * len(parts))(*parts)
+    out = kc.kc_pool_sums()
+    kc._check(kc.load().kc_combine_sums(arr, len(parts), ctypes.byref(out)), "kc_combine_sums")
+    return _as_dict(out)
 
 
 def estimate_from_sums(sums: dict, twom: int, unit_weights: bool = True) -> float:
-    """K_hat = sum f / (2m omega) (exact numerator) or sum w f / (2m sum w)."""
-    if unit_weights:
-        return sums["f_sum"] / (twom * sums["count"])
-    return sums["wf"] / sums["w"]
+    """K_hat of (combined) pool sums, computed by kc_estimate_from_sums."""
+    import ctypes
+
+    from . import kc
+
+    k = ctypes.c_double()
+    kc._check(kc.load().kc_estimate_from_sums(ctypes.byref(_as_struct(sums)), int(twom),
+                                             1 if unit_weights else 0, ctypes.byref(k)),
+             "kc_estimate_from_sums")
+    return k.value
+
+
+def f_sum(sums: dict) -> int:
+    """The exact int128 sum of f as a Python integer (for reporting)."""
+    return int(sums["f_sum_hi"]) * (1 << 64) + (int(sums["f_sum_lo"]) & ((1 << 64) - 1))
 
 
 def max_over_ranks(x: float, group=None) -> float:

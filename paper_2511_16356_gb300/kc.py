@@ -86,6 +86,12 @@ class kc_stats_t(ctypes.Structure):
         return d
 
 
+class kc_pool_sums(ctypes.Structure):
+    _fields_ = [("f_sum_hi", ctypes.c_int64), ("f_sum_lo", ctypes.c_uint64),
+                ("wf_sum", ctypes.c_double), ("w_sum", ctypes.c_double),
+                ("x2_sum", ctypes.c_double), ("count", ctypes.c_int64)]
+
+
 class kc_server_config(ctypes.Structure):
     _fields_ = [("struct_size", ctypes.c_uint32), ("workers", ctypes.c_int32),
                 ("budget_bytes", ctypes.c_int64), ("request_bytes", ctypes.c_int64)]
@@ -129,6 +135,10 @@ _SIGS = {
                                          _P, _P]),
     "kc_stats": (ctypes.c_int, [_P, ctypes.POINTER(kc_stats_t)]),
     "kc_reset_timers": (ctypes.c_int, [_P]),
+    "kc_combine_sums": (ctypes.c_int, [ctypes.POINTER(kc_pool_sums), ctypes.c_int32,
+                                       ctypes.POINTER(kc_pool_sums)]),
+    "kc_estimate_from_sums": (ctypes.c_int, [ctypes.POINTER(kc_pool_sums), ctypes.c_int64,
+                                             ctypes.c_int32, ctypes.POINTER(ctypes.c_double)]),
     "kc_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "kc_last_error": (ctypes.c_char_p, [_P]),
     "kc_server_config_default": (None, [ctypes.POINTER(kc_server_config)]),

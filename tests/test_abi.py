@@ -181,3 +181,22 @@ def test_binding_struct_sizes_match_the_c_compiler(tmp_path):
     got = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True,
                                           check=True).stdout.split()]
     assert got == [ctypes.sizeof(getattr(kc, n)) for n in names]
+
+
+def test_noalloc_rejects_bad_arguments_before_device_work(lib):
+    """kc_wilson_noalloc validates its sizes before it touches a device: sample
+    ids past 2^32 (including a count whose sum with the first id would overflow
+    int64), negative counts and oversized requests are refused, and zero trees
+    is a no-op.  The pointers are never dereferenced on these paths."""
+    from paper_2511_16356_gb300 import kc
+
+    p = 256  # a non-null dummy address, never read
+    call = lambda n, first, cnt: kc.STATUS[lib.kc_wilson_noalloc(n, p, p, 0, 1, first, cnt, 0,
+                                                                  p, p, p, None)]
+    assert call(10, (1 << 32) - 4, 5) == "KC_ERR_INVALID_ARG"
+    assert call(10, 1 << 40, 1) == "KC_ERR_INVALID_ARG"
+    assert call(10, 7, (1 << 63) - 2) == "KC_ERR_INVALID_ARG"
+    assert call(10, 0, -1) == "KC_ERR_INVALID_ARG"
+    assert call(1, 0, 1) == "KC_ERR_INVALID_ARG"
+    assert call(10, 0, 0) == "KC_OK"
+    assert call(1 << 20, 0, 9) == "KC_ERR_SCRATCH_LIMIT"

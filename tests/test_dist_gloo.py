@@ -36,8 +36,9 @@ def _rank_sums(rank, world):
     f, _ = O.sample_batch(g, t0, 9, base, PER_RANK, threads=1)
     twom = 2 * g.m
     x = f.astype(np.float64) / twom
-    return g, {"f_sum": int(sum(int(v) for v in f)), "wf": float(x.sum()), "w": float(PER_RANK),
-               "x2": float((x * x).sum()), "count": PER_RANK}
+    fs = int(sum(int(v) for v in f))
+    return g, {"f_sum_hi": fs >> 64, "f_sum_lo": fs & ((1 << 64) - 1), "wf_sum": float(x.sum()),
+               "w_sum": float(PER_RANK), "x2_sum": float((x * x).sum()), "count": PER_RANK}
 
 
 def _worker(rank, world, port, q):
@@ -48,7 +49,7 @@ def _worker(rank, world, port, q):
     comb = kd.combine_pool_sums(local)
     k = kd.estimate_from_sums(comb, 2 * g.m)
     t = kd.max_over_ranks(float(rank + 1))
-    q.put((rank, comb["f_sum"], comb["count"], k, t, kd.rank_sample_base(rank, world, IDS)))
+    q.put((rank, kd.f_sum(comb), comb["count"], k, t, kd.rank_sample_base(rank, world, IDS)))
     dist.barrier()
     dist.destroy_process_group()
 
@@ -83,13 +84,35 @@ def test_two_gloo_ranks_combine_exactly():
     assert res[0][3] == pytest.approx(want / (2 * g.m * 2 * PER_RANK), rel=1e-15)
 
 
-def test_int128_limbs_roundtrip_negative_and_large():
-    for v in [0, 1, -1, (1 << 100) + 12345, -(1 << 90) - 7]:
-        limbs = [(v >> (32 * k)) & 0xFFFFFFFF for k in range(4)]
-        back = sum(limbs[k] << (32 * k) for k in range(4))
-        if back >= 1 << 127:
-            back -= 1 << 128
-        assert back == v
+def _sums(v, count=1, wf=0.0, w=1.0, x2=0.0):
+    return {"f_sum_hi": v >> 64, "f_sum_lo": v & ((1 << 64) - 1), "wf_sum": wf, "w_sum": w,
+            "x2_sum": x2, "count": count}
+
+
+def test_c_combination_is_exact_for_negative_and_large_sums():
+    """kc_combine_sums adds the int128 limbs exactly (carries across the low
+    limb, negative values) and the counts; kc_estimate_from_sums divides the
+    exact sum once."""
+    from paper_2511_16356_gb300 import build as kbuild
+    from paper_2511_16356_gb300 import kc
+
+    kbuild.build()
+    vals = [0, 1, -1, (1 << 100) + 12345, -(1 << 90) - 7, (1 << 64) - 1, 1 << 63]
+    parts = [kd._as_struct(_sums(v, count=3)) for v in vals]
+    arr = (kc.kc_pool_sums * len(parts))(*parts)
+    out = kc.kc_pool_sums()
+    import ctypes
+
+    assert kc.load().kc_combine_sums(arr, len(parts), ctypes.byref(out)) == 0
+    comb = kd._as_dict(out)
+    assert kd.f_sum(comb) == sum(vals) and comb["count"] == 3 * len(vals)
+    k = kd.estimate_from_sums(_sums(10 ** 20 + 7, count=9), 2 * 1000)
+    assert k == (10 ** 20 + 7) / (2000 * 9)
+    assert kd.estimate_from_sums(_sums(0, count=2, wf=3.0, w=4.0), 10, unit_weights=False) == 0.75
+    # an int128 overflow is refused
+    big = [kd._as_struct(_sums((1 << 126) + 1)), kd._as_struct(_sums((1 << 126) + 1))]
+    arr2 = (kc.kc_pool_sums * 2)(*big)
+    assert kc.load().kc_combine_sums(arr2, 2, ctypes.byref(out)) == 1
 
 
 def test_rank_bases_are_disjoint_and_bounded():

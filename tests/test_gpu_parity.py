@@ -214,8 +214,6 @@ def test_hoeffding_rule_draws_theorem5_trees(name, eps):
     assert k == pytest.approx(O.estimate_fixed(f, 2 * g.m), rel=1e-12)
 
 
-@pytest.mark.skip(reason="rejection by walk length has not yet run on a GPU: enable after a "
-                         "first supervised run")
 @pytest.mark.parametrize("name,trees", [("grid17x13", 500), ("er300", 500), ("cl3000", 500),
                                         ("cl80000", 96)])
 def test_rejection_by_walk_length_matches_oracle(name, trees):

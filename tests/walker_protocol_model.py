@@ -12,9 +12,6 @@ The departure of u on its k-th visit uses the oracle's bounded Philox draw, so
 by cycle popping the model must reproduce the oracle's sequential tree, step
 count and depths for every start order and walker count.  It documents and
 checks the protocol's design on the CPU; it is not the device code.
-
-    python tests/walker_protocol_model.py 100 64        # tail study: grid side, trees
-    python tests/walker_protocol_model.py phases 120 300 # waits and departures per iteration
 """
 import numpy as np
 
@@ -229,60 +226,3 @@ def walk_tree(g, r, seed, sample, sorder, lanes=32, max_iter=10 ** 7, phases=Non
     parent = nxt.copy()
     parent[r] = -1
     return parent.astype(np.int32), steps, depth, order, it
-
-
-def tail_study(side: int, trees: int, lanes_list=(32, 128)):
-    """Iterations of each tree of a wave on a perturbed grid, for the slowest
-    tree against the median one (the wave lasts as long as its slowest tree)."""
-    import oracle as O
-    from paper_2511_16356_gb300 import synth as S
-
-    g = S.grid_perturbed(side, side, 0.25, 1)
-    t0 = O.tau0(g)
-    sorder = np.random.default_rng(0).permutation(g.n)
-    steps = []
-    its = {L: [] for L in lanes_list}
-    for sample in range(trees):
-        for L in lanes_list:
-            _, st, _, _, it = walk_tree(g, t0.r, 5, sample, sorder, lanes=L)
-            its[L].append(it)
-        steps.append(st)
-    steps = np.array(steps)
-    slow, med = int(np.argmax(steps)), int(np.argsort(steps)[len(steps) // 2])
-    print(f"{side}x{side} grid, {trees} trees: slowest S / median S = {steps[slow] / steps[med]:.2f}")
-    for L in lanes_list:
-        it = np.array(its[L])
-        alpha = np.polyfit(np.log(steps), np.log(it), 1)[0]  # iterations ~ S^alpha
-        print(f"  {L} lanes: slowest tree {it[slow]} iterations ({steps[slow] / it[slow]:.1f} "
-              f"departures each), median tree {it[med]} ({steps[med] / it[med]:.1f}); "
-              f"ratio {it[slow] / it[med]:.1f}; iterations ~ S^{alpha:.2f} over the trees")
-
-
-def phase_study(sides, lanes: int = 32):
-    """Departures per iteration and the share of lane-iterations spent waiting
-    on another walker's path, for one tree on each perturbed grid."""
-    import oracle as O
-    from paper_2511_16356_gb300 import synth as S
-
-    for side in sides:
-        g = S.grid_perturbed(side, side, 0.25, 1)
-        t0 = O.tau0(g)
-        sorder = np.random.default_rng(0).permutation(g.n)
-        counts = [0] * 8
-        _, st, _, _, it = walk_tree(g, t0.r, 5, 0, sorder, lanes=lanes, phases=counts)
-        busy = sum(counts) - counts[DONE]
-        print(f"{side}x{side} grid, {lanes} lanes: {st / it:.2f} departures per iteration, "
-              f"{counts[WAIT] / busy:.0%} of lane-iterations waiting, "
-              f"{counts[WALK] / busy:.0%} walking", flush=True)
-
-
-if __name__ == "__main__":
-    import os
-    import sys
-
-    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
-    if len(sys.argv) > 1 and sys.argv[1] == "phases":
-        phase_study([int(a) for a in sys.argv[2:]] or [60, 120])
-    else:
-        tail_study(int(sys.argv[1]) if len(sys.argv) > 1 else 100,
-                   int(sys.argv[2]) if len(sys.argv) > 2 else 64)
