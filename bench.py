@@ -251,6 +251,150 @@ def run_reference(args):
 WALKER_NAMES = {1: "lane", 2: "warp", 3: "hybrid"}
 
 
+def golden_K(workload: str):
+    """The stored reference Kemeny constant of a workload (tests/golden/, written
+    by committed scripts that call only the oracle): (K, standard error), the
+    error 0 for exact values; None when no value is stored."""
+    fn = os.path.join(ROOT, "tests", "golden", f"{workload}_K.txt")
+    if not os.path.exists(fn):
+        return None
+    for line in open(fn):
+        line = line.strip()
+        if line and not line.startswith("#"):
+            vals = [float(x) for x in line.split()]
+            return vals[0], (vals[1] if len(vals) > 1 else 0.0)
+    return None
+
+
+def timed_sampling(G, T: int, steps: int, seed: int, stream, flush) -> list:
+    """`steps` timed kc_sample calls of T trees each, L2 flushed before each;
+    CUDA events on the handle's stream.  Returns the per-step milliseconds."""
+    import torch
+
+    step_ms = []
+    for _ in range(steps):
+        flush.fill_(1)  # evict L2 between timed steps
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        G.sample(seed, T)
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+    return step_ms
+
+
+def phase_roofline(kc, st: dict, n: int, trees: int, steps_total: int, tot_ms: float,
+                   walker_traffic=None) -> tuple:
+    """The dominant phase of the timed steps (kc_stats' CUDA-event phase timers)
+    and its roofline object: algorithmic bytes per launch over the mean launch
+    time, against the measured HBM copy peak; plus the whole path's fraction."""
+    bit = st["ttf_variant"] == kc.KC_TTF_BIT
+    phases = {
+        "wilson": (st["ms_wilson"], st["launches_wilson"]),
+        "traverse": (st["ms_traverse"], st["launches_traverse"]),
+        "ttf_bit" if bit else "ttf_scan": (st["ms_ttf"], st["launches_ttf"]),
+    }
+    dom = max(phases, key=lambda k: phases[k][0])
+    dom_ms, dom_launches = phases[dom]
+    alg = algorithmic_bytes(dom, n, st["ecc"], trees, steps_total)
+    peak, peak_kind = _peaks()
+    per_launch_bytes = alg / max(1, dom_launches)
+    per_launch_s = max(dom_ms, 1e-9) / 1000.0 / max(1, dom_launches)
+    achieved = per_launch_bytes / per_launch_s / 1e9
+    kernel_name = {"wilson": {kc.KC_WALK_LANE: "k_wilson", kc.KC_WALK_WARP: "k_wilson_warp",
+                              kc.KC_WALK_HYBRID: "k_wilson+k_wilson_warp"}[st["walker"]],
+                   "traverse": "traversal passes",
+                   "ttf_bit": "k_ttf_bit", "ttf_scan": "k_ttf_scan"}[dom]
+    traffic = None
+    if walker_traffic is not None and dom == "wilson":
+        traffic = walker_traffic * steps_total / max(1, dom_launches)
+    roof = {"bound": "hbm", "kernel": kernel_name, "achieved": achieved, "peak": peak,
+            "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": traffic,
+            "algorithmic_bytes_per_launch": per_launch_bytes,
+            "mean_launch_ms": per_launch_s * 1000.0,
+            # the whole sampling path over the timed steps (walk, traversal,
+            # f), against the same peak
+            "path_frac": path_bytes(n, st["ecc"], bit, trees, steps_total)
+                         / (tot_ms / 1000.0) / 1e9 / peak}
+    phase_ms = {k: round(v[0], 3) for k, v in phases.items()}
+    phase_ms["wave_init"] = round(st["ms_wave_init"], 3)
+    phase_ms["reduce"] = round(st["ms_reduce"], 3)
+    return dom, roof, phase_ms
+
+
+def time_to_eps(kc, g, cfg, eps: float, delta: float, batch: int, stream, workload: str) -> dict:
+    """Wall time of kc_estimate(eps, delta) on a fresh handle (tau0 precomputed,
+    inputs resident), the trees it drew, K_hat and its error against the stored
+    reference."""
+    import torch
+
+    cfg2 = kc.kc_config_default()
+    for f, _ in kc.kc_config._fields_:
+        setattr(cfg2, f, getattr(cfg, f))
+    cfg2.batch_trees = batch
+    cfg2.reject_steps = 0
+    H = kc.KemenyGraph.from_graph(g, cfg2, stream=stream.cuda_stream)
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    k_hat = H.estimate(eps, delta)
+    tte = time.perf_counter() - t
+    sh = H.stats()
+    drawn = H.samples(0, sh["pool_trees"])
+    peak, _ = _peaks()
+    tte_bytes = path_bytes(g.n, sh["ecc"], sh["ttf_variant"] == kc.KC_TTF_BIT,
+                           sh["pool_trees"], int(drawn["steps"].sum()))
+    H.close()
+    out = {"value": tte, "unit": "s", "eps": eps, "delta": delta, "trees": sh["pool_trees"],
+           "K": k_hat, "batch_trees": int(batch),
+           "roofline_frac": tte_bytes / tte / 1e9 / peak,
+           "rule": "CLT: z s/sqrt(w) <= eps K (1-eps)"}
+    ref = golden_K(workload)
+    if ref is not None:
+        out["K_ref"] = ref[0]
+        out["K_ref_se"] = ref[1]
+        out["rel_err"] = (k_hat - ref[0]) / ref[0]
+    return out
+
+
+def other_workload_leg(args, kc, stream, flush, name: str, T: int, steps: int, warmup: int,
+                       delta: float) -> dict:
+    """A further static workload at its stated size: trees/s over `steps` timed
+    kc_sample calls of T trees (after `warmup` untimed ones), the dominant
+    kernel's roofline, and time to eps with K_hat against the stored reference."""
+    import torch
+
+    from paper_2511_16356_gb300 import synth as S
+
+    g = S.workload(name)
+    cfg = kc.kc_config_default()
+    cfg.keep_trees = 0
+    G = kc.KemenyGraph.from_graph(g, cfg, stream=stream.cuda_stream)
+    G.reserve(T * (warmup + steps))
+    for _ in range(warmup):
+        G.sample(args.seed, T)
+    torch.cuda.synchronize()
+    kc.kc_reset_timers(G.h)
+    pool0 = G.stats()["pool_trees"]
+    step_ms = timed_sampling(G, T, steps, args.seed, stream, flush)
+    tot_ms = float(sum(step_ms))
+    st = G.stats()
+    smp = G.samples(pool0, st["pool_trees"] - pool0)
+    steps_total = int(smp["steps"].sum())
+    dom, roof, phase_ms = phase_roofline(kc, st, g.n, T * steps, steps_total, tot_ms)
+    G.close()
+    out = {"workload": S.WORKLOADS.get(name, name), "n": g.n, "m": g.m, "ecc": st["ecc"],
+           "trees_per_step": T, "steps": steps, "warmup": warmup,
+           "value": T * steps / (tot_ms / 1000.0), "unit": "trees/s",
+           "ms_per_step": tot_ms / steps, "roofline": roof, "phase_ms": phase_ms,
+           "steps_per_tree": steps_total / (T * steps),
+           "ttf": "BIT" if st["ttf_variant"] == kc.KC_TTF_BIT else "SCAN"}
+    out["time_to_eps"] = time_to_eps(kc, g, cfg, args.eps, delta, 1024, stream, name)
+    return out
+
+
+
 def serve_workload(n_graphs: int, n_max: int, seed: int = 3):
     """Mixed resident graphs: ER, perturbed grids and Chung-Lu graphs with n
     log-uniform on [1e3, n_max] (seeded)."""
@@ -488,6 +632,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-tte", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--no-other", action="store_true",
+                    help="skip the other static workloads (er2000, cl4m)")
     ap.add_argument("--serve-graphs", type=int, default=48)
     ap.add_argument("--serve-nmax", type=float, default=3e4)
     ap.add_argument("--serve-queries", type=int, default=96)
@@ -564,16 +710,7 @@ def main():
     barrier(dist)
     torch.cuda.synchronize()
     clocks.start()
-    step_ms = []
-    for _ in range(args.steps):
-        flush.fill_(1)  # evict L2 between timed steps
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        G.sample(args.seed, T)
-        e1.record(stream)
-        e1.synchronize()
-        step_ms.append(e0.elapsed_time(e1))
+    step_ms = timed_sampling(G, T, args.steps, args.seed, stream, flush)
     torch.cuda.synchronize()
     clk = clocks.stop()
     barrier(dist)
@@ -584,33 +721,15 @@ def main():
     samples = G.samples(pool0, st["pool_trees"] - pool0)
     steps_total = int(samples["steps"].sum())
     trees_timed = T * args.steps
-
-    # dominant phase, roofline from its CUDA-event time inside kc_sample
-    phases = {
-        "wilson": (st["ms_wilson"], st["launches_wilson"]),
-        "traverse": (st["ms_traverse"], st["launches_traverse"]),
-        "ttf_bit" if st["ttf_variant"] == kc.KC_TTF_BIT else "ttf_scan":
-            (st["ms_ttf"], st["launches_ttf"]),
-    }
-    dom = max(phases, key=lambda k: phases[k][0])
-    dom_ms, dom_launches = phases[dom]
-    alg = algorithmic_bytes(dom, n, st["ecc"], trees_timed, steps_total)
-    peak, peak_kind = _peaks()
-    per_launch_bytes = alg / max(1, dom_launches)
-    per_launch_s = dom_ms / 1000.0 / max(1, dom_launches)
-    achieved = per_launch_bytes / per_launch_s / 1e9
+    traffic_per_step = (WILSON_WARP_GRID_DRAM_BYTES_PER_STEP
+                        if st["walker"] == kc.KC_WALK_WARP and args.workload.startswith("grid")
+                        else None)
+    dom, roof, phase_ms = phase_roofline(kc, st, n, trees_timed, steps_total, tot_ms,
+                                         traffic_per_step)
+    roof["traffic_basis"] = (None if roof["traffic"] is None else
+                             "ncu dram bytes per departure on grid300x300 (1000 trees) x "
+                             "departures")
     launches = sum(st[k] for k in st if k.startswith("launches_") and k != "launches_setup")
-    kernel_name = {"wilson": {kc.KC_WALK_LANE: "k_wilson", kc.KC_WALK_WARP: "k_wilson_warp",
-                              kc.KC_WALK_HYBRID: "k_wilson+k_wilson_warp"}[st["walker"]],
-                   "traverse": "k_bottom_up/k_sibling_offsets/k_top_down",
-                   "ttf_bit": "k_ttf_bit", "ttf_scan": "k_ttf_scan"}[dom]
-    traffic = None
-    if (WILSON_WARP_GRID_DRAM_BYTES_PER_STEP is not None and dom == "wilson"
-            and st["walker"] == kc.KC_WALK_WARP and args.workload.startswith("grid")):
-        traffic = WILSON_WARP_GRID_DRAM_BYTES_PER_STEP * steps_total / max(1, dom_launches)
-    phase_ms = {k: round(v[0], 3) for k, v in phases.items()}
-    phase_ms["wave_init"] = round(st["ms_wave_init"], 3)
-    phase_ms["reduce"] = round(st["ms_reduce"], 3)
 
     out = {
         "metric": "trees/sec", "value": value, "unit": "trees/s", "n_gpus": ws,
@@ -625,18 +744,7 @@ def main():
                    "ttf": "BIT" if st["ttf_variant"] == kc.KC_TTF_BIT else "SCAN",
                    "walker": WALKER_NAMES[st["walker"]],
                    "trees_in_flight": st["trees_in_flight"]},
-        "roofline": {"bound": "hbm", "kernel": kernel_name, "achieved": achieved, "peak": peak,
-                     "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": traffic,
-                     "traffic_basis": None if traffic is None else
-                     "ncu dram bytes per departure on grid300x300 (1000 trees) x departures",
-                     "algorithmic_bytes_per_launch": per_launch_bytes,
-                     "mean_launch_ms": per_launch_s * 1000.0,
-                     # the whole sampling path over the timed steps (walk,
-                     # traversal, f), against the same peak
-                     "path_frac": path_bytes(n, st["ecc"], st["ttf_variant"] == kc.KC_TTF_BIT,
-                                             trees_timed, steps_total)
-                                  / (tot_ms / 1000.0) / 1e9 / peak},
+        "roofline": roof,
         "phase_ms": phase_ms,
         "rejection": None if reject is None else
         dict(reject, trees_rejected=int(st["trees_rejected"] - rej0),
@@ -650,32 +758,20 @@ def main():
 
     # ---- time to eps on a fresh handle (tau0 precomputed, inputs resident)
     if not args.no_tte and rank == 0:
-        cfg2 = kc.kc_config_default()
-        cfg2.keep_trees = 0
-        cfg2.step_cap = cfg.step_cap
-        cfg2.walker = cfg.walker
-        cfg2.hybrid_prefix_permille = cfg.hybrid_prefix_permille
-        cfg2.hybrid_tail_permille = cfg.hybrid_tail_permille
         # batches of one resident wave where trees are long (deep tau0: a wave
         # lasts about as long as its slowest tree, so a wave of 1024 costs
         # about what a full one does), 1024 trees where waves are throughput-bound
         deep = st["ttf_variant"] == kc.KC_TTF_BIT and st["walker"] == kc.KC_WALK_WARP
-        cfg2.batch_trees = max(1024, st["resident_trees"]) if deep else 1024
-        H = kc.KemenyGraph.from_graph(g, cfg2, stream=stream.cuda_stream)
-        torch.cuda.synchronize()
-        t = time.perf_counter()
-        k_hat = H.estimate(args.eps, args.delta)
-        tte = time.perf_counter() - t
-        sh = H.stats()
-        drawn = H.samples(0, sh["pool_trees"])
-        tte_bytes = path_bytes(n, sh["ecc"], sh["ttf_variant"] == kc.KC_TTF_BIT,
-                               sh["pool_trees"], int(drawn["steps"].sum()))
-        out["time_to_eps"] = {"value": tte, "unit": "s", "eps": args.eps, "delta": args.delta,
-                              "trees": sh["pool_trees"], "K": k_hat,
-                              "batch_trees": int(cfg2.batch_trees),
-                              "roofline_frac": tte_bytes / tte / 1e9 / peak,
-                              "rule": "CLT: z s/sqrt(w) <= eps K (1-eps)"}
-        H.close()
+        batch = max(1024, st["resident_trees"]) if deep else 1024
+        out["time_to_eps"] = time_to_eps(kc, g, cfg, args.eps, args.delta, batch, stream,
+                                         args.workload)
+
+    # ---- the other static workloads at their stated sizes (rank 0)
+    if not args.no_other and rank == 0:
+        out["other_workloads"] = {
+            "er2000": other_workload_leg(args, kc, stream, flush, "er2000", 2000, 20, 5, 0.05),
+            "cl4m": other_workload_leg(args, kc, stream, flush, "cl4m", 10000, 2, 2, 0.01),
+        }
 
     # ---- end to end through the C ABI with host buffers
     if not args.no_e2e:
