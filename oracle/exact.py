@@ -14,7 +14,7 @@ import numpy as np
 
 __all__ = [
     "laplacian_dense", "K_dense", "K_grounded", "K_eq3", "K_closed", "K_tree_graph",
-    "trace_green", "resistance", "resistance_all_edges", "spanning_trees", "kirchhoff_count",
+    "trace_green", "resistance", "resistance_sparse", "resistance_all_edges", "spanning_trees", "kirchhoff_count",
     "orient", "f_literal", "two_forests", "K_forest_formula", "hoeffding_trees",
     "K_torus", "K_hypercube",
 ]
@@ -136,6 +136,29 @@ def resistance(g, u: int, v: int) -> float:
     X = np.linalg.inv(L[np.ix_(keep, keep)])
     idx = int(v) - (1 if v > u else 0)
     return float(X[idx, idx])
+
+
+def resistance_sparse(g, u: int, v: int, rtol: float = 1e-13) -> float:
+    """Effective resistance (e_u - e_v)^T L^+ (e_u - e_v) for graphs too large
+    for a dense inverse: the Laplacian grounded at u (SPD) solved for e_v by
+    scipy's conjugate gradients with the diagonal preconditioner, R = x_v."""
+    import scipy.sparse as sp
+    from scipy.sparse.linalg import LinearOperator, cg
+
+    n = g.n
+    rows = np.repeat(np.arange(n), np.diff(g.row_off))
+    A = sp.csr_matrix((np.ones(len(g.col)), (rows, g.col)), shape=(n, n))
+    L = sp.diags(np.asarray(A.sum(axis=1)).ravel()) - A
+    keep = np.arange(n) != u
+    Lg = L[keep][:, keep].tocsr()
+    b = np.zeros(n - 1)
+    b[int(v) - (1 if v > u else 0)] = 1.0
+    dinv = 1.0 / Lg.diagonal()
+    M = LinearOperator(Lg.shape, matvec=lambda x: dinv * x)
+    x, info = cg(Lg, b, rtol=rtol, atol=0.0, maxiter=50 * n + 1000, M=M)
+    if info != 0:
+        raise RuntimeError("CG did not converge")
+    return float(x[int(v) - (1 if v > u else 0)])
 
 
 def resistance_all_edges(g) -> dict:

@@ -705,19 +705,6 @@ void traverse_tau0(kc_graph *g, int &launches) {
 // ===========================================================================
 // Sample maintenance (Algorithms 2 and 3)
 // ===========================================================================
-// insert or erase (u, v) and (v, u) in a CSR kept sorted row by row
-void mutate_csr(std::vector<int64_t> &ro, std::vector<int32_t> &col, int32_t u, int32_t v,
-                bool insert) {
-    const int64_t n = (int64_t)ro.size() - 1;
-    for (int pass = 0; pass < 2; ++pass) {
-        const int32_t a = pass == 0 ? u : v, b = pass == 0 ? v : u;
-        auto first = col.begin() + ro[(size_t)a], last = col.begin() + ro[(size_t)a + 1];
-        auto it = std::lower_bound(first, last, b);
-        if (insert) col.insert(it, b); else col.erase(it);
-        for (int64_t x = a + 1; x <= n; ++x) ro[(size_t)x] += insert ? 1 : -1;
-    }
-}
-
 // |f| <= 4 m^2 ecc(r) (Theorem 5's proof) must stay below 2^62 for the int64 f
 bool f_may_overflow(int64_t m, int32_t ecc) {
     const long double bound = 4.0L * (long double)m * (long double)m * (long double)ecc;
@@ -754,22 +741,57 @@ kc_status validate_batch(kc_graph *g, const kc_edge_op *ops, int64_t n_ops) {
     return KC_OK;
 }
 
-// copy the host CSR to the device and rebuild the walk records and degrees
-void upload_graph(kc_graph *g) {
-    const int64_t n = g->n, twom = g->h_row_off[(size_t)n];
-    if ((size_t)twom > g->col_cap) {
+// One op on the device CSR (rows kept sorted), then the walk records and
+// degrees of the changed graph; the host copy of the CSR is refreshed once per
+// batch (sync_host_csr).  Nothing goes through the host per op but the check
+// that the edit applied.
+void edit_graph(kc_graph *g, int32_t u, int32_t v, bool insert) {
+    const int64_t twom = 2 * g->m;
+    const size_t need = (size_t)twom + 2;
+    if (need > g->col_cap) {
+        const size_t cap = need + need / 8 + 64;
+        int32_t *q = nullptr;
+        dalloc(g, &q, cap);
+        KC_CK(g, cudaMemcpyAsync(q, g->d_col, sizeof(int32_t) * (size_t)twom,
+                                 cudaMemcpyDeviceToDevice, g->stream));
+        KC_CK(g, cudaStreamSynchronize(g->stream));
         dfree(g->d_col);
-        const size_t cap = (size_t)twom + (size_t)twom / 8 + 64;
-        dalloc(g, &g->d_col, cap);
+        g->d_col = q;
         g->col_cap = cap;
     }
-    KC_CK(g, cudaMemcpyAsync(g->d_row_off, g->h_row_off.data(), sizeof(int64_t) * (n + 1),
-                             cudaMemcpyHostToDevice, g->stream));
-    KC_CK(g, cudaMemcpyAsync(g->d_col, g->h_col.data(), sizeof(int32_t) * twom,
-                             cudaMemcpyHostToDevice, g->stream));
-    g->m = twom / 2;
+    if (need > g->edit_cap) {
+        dfree(g->d_edit);
+        const size_t cap = std::max(need + need / 8 + 64, g->col_cap);
+        dalloc(g, &g->d_edit, cap);
+        g->edit_cap = cap;
+    }
+    int64_t *pos = (int64_t *)g->d_scratch + 64;  // 3 words past the reduction sums
+    KC_CK(g, launch_csr_edit(g->n, twom, g->d_row_off, g->d_col, g->d_edit, pos, u, v, insert,
+                             g->stream));
+    int64_t hp[3] = {0, 0, 0};
+    KC_CK(g, copy_sync(g, hp, pos, sizeof(hp), cudaMemcpyDeviceToHost));
+    if (hp[2]) {
+        g->last_error = "kc_update: the device graph does not match the validated batch";
+        throw Fail{KC_ERR_CUDA};
+    }
+    g->m += insert ? 1 : -1;
+    g->host_csr_stale = true;
     KC_CK(g, launch_build_records(view_of(g), g->d_rec, g->d_deg, g->stream));
-    KC_CK(g, cudaStreamSynchronize(g->stream));
+    g->t_update.launches += 4;
+}
+
+// the host copy of the CSR (batch validation reads it) from the device
+void sync_host_csr(kc_graph *g) {
+    if (!g->host_csr_stale) return;
+    const int64_t n = g->n;
+    g->h_row_off.resize((size_t)n + 1);
+    KC_CK(g, copy_sync(g, g->h_row_off.data(), g->d_row_off, sizeof(int64_t) * (size_t)(n + 1),
+                       cudaMemcpyDeviceToHost));
+    const int64_t twom = g->h_row_off[(size_t)n];
+    g->h_col.resize((size_t)twom);
+    KC_CK(g, copy_sync(g, g->h_col.data(), g->d_col, sizeof(int32_t) * (size_t)twom,
+                       cudaMemcpyDeviceToHost));
+    g->host_csr_stale = false;
 }
 
 struct UpdBuf {
@@ -952,16 +974,16 @@ double weight_sum(kc_graph *g, const std::vector<uint8_t> &flags, int which) {
 }
 
 void apply_insert(kc_graph *g, int32_t u, int32_t v, int32_t mode, double r_given) {
-    mutate_csr(g->h_row_off, g->h_col, u, v, true);
-    upload_graph(g);
+    edit_graph(g, u, v, true);
     // the BIT kernel holds 2m in 32 bits; the scan gives the same f on any graph
     if (g->ttf_variant == KC_TTF_BIT && 2 * g->m >= ((int64_t)1 << 31)) g->ttf_variant = KC_TTF_SCAN;
     double R = r_given;
     if (g->cfg.r_source != KC_R_GIVEN) {
         int nl = 0;
         int64_t iters = 0;
-        KC_CK(g, resistance_cg(view_of(g), u, v, 1e-13, 50 * g->n + 1000, &R, &iters, &nl,
-                               g->stream));
+        if (!g->d_cg) dalloc(g, &g->d_cg, cg_scratch_doubles(g->n));
+        KC_CK(g, resistance_cg(view_of(g), u, v, 1e-13, 50 * g->n + 1000, g->d_cg, &R, &iters,
+                               &nl, g->stream, &g->cg_graph));
         g->t_update.launches += nl;
         g->last_cg_iters = iters;
     }
@@ -1014,8 +1036,7 @@ void apply_delete(kc_graph *g, int32_t u, int32_t v, int32_t mode) {
     const bool tau0_hit = (pu == v) || (pv == u);
     double w_org = 0.0;
     if (mode == KC_UPDATE_ISM) w_org = weight_sum(g, flags, 0);
-    mutate_csr(g->h_row_off, g->h_col, u, v, false);
-    upload_graph(g);
+    edit_graph(g, u, v, false);
     if (tau0_hit) {
         int nl = 0;
         build_tau0(g, nl);
@@ -1607,6 +1628,9 @@ kc_status kc_graph_destroy(kc_graph *g) {
     dfree(g->d_parents);
     dfree(g->d_ws);
     if (g->d_ub) cudaFree(g->d_ub);
+    dfree(g->d_edit);
+    dfree(g->d_cg);
+    cg_graph_release(g->cg_graph);
     dfree(g->d_stack);
     dfree(g->d_sorder);
     dfree(g->d_err);
@@ -2188,7 +2212,13 @@ kc_status kc_update(kc_graph *g, const kc_edge_op *ops, int64_t n_ops, int32_t m
         float ms = 0.f;
         KC_CK(g, cudaEventElapsedTime(&ms, g->ev0, g->ev1));
         g->t_update.ms += ms;
+        sync_host_csr(g);
     } catch (Fail &f) {
+        // ops applied before the failure stay applied: keep the host copy in step
+        try {
+            sync_host_csr(g);
+        } catch (Fail &) {
+        }
         return f.st;
     }
     return KC_OK;

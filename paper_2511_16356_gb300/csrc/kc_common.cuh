@@ -185,6 +185,15 @@ struct PhaseTimer {
     int64_t launches = 0;
 };
 
+// A captured chunk of conjugate-gradient iterations (k8_resistance.cu) and the
+// pointers and size it was captured for.
+struct CgGraph {
+    cudaGraphExec_t exec = nullptr;
+    const void *key[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    int launches = 0;  // kernel launches one replay stands for
+    cudaStream_t capture_stream = nullptr;
+};
+
 }  // namespace kc
 
 struct kc_graph {
@@ -230,6 +239,11 @@ struct kc_graph {
     void *d_ub = nullptr;           // update buffers: slots, factors, selection, flags
     size_t ub_bytes = 0;
     size_t col_cap = 0;             // capacity of d_col (entries)
+    int32_t *d_edit = nullptr;      // scratch column array of a graph edit
+    size_t edit_cap = 0;
+    double *d_cg = nullptr;         // conjugate-gradient vectors of R(u, v)
+    kc::CgGraph cg_graph;           // their captured iteration chunk
+    bool host_csr_stale = false;    // h_row_off / h_col behind the device CSR
     int64_t ws_trees = 0;
     uint32_t *d_err = nullptr;
     void *d_scratch = nullptr;      // small reduction scratch
@@ -390,9 +404,19 @@ cudaError_t launch_weight_sums(const double *w, const uint8_t *flag, int64_t P, 
 cudaError_t launch_scatter_results(const int64_t *slot, int64_t B, const int64_t *f,
                                    const int64_t *steps, const int64_t *sids, int64_t *pool_f,
                                    int64_t *pool_steps, int64_t *pool_sid, cudaStream_t s);
-// R(u, v) = (e_u - e_v)^T L^+ (e_u - e_v) by Jacobi-preconditioned FP64 CG.
+// R(u, v) = (e_u - e_v)^T L^+ (e_u - e_v) by Jacobi-preconditioned FP64 CG, in
+// caller-owned scratch of cg_scratch_doubles(n) doubles.  With `cache`, the
+// iterations between two residual checks run as one captured CUDA graph, kept
+// in the cache for later calls on the same CSR, scratch and n.
+void cg_graph_release(CgGraph &c);
+size_t cg_scratch_doubles(int64_t n);
 cudaError_t resistance_cg(const GraphView &g, int32_t u, int32_t v, double tol, int64_t max_iter,
-                          double *R_out, int64_t *iters_out, int *launches, cudaStream_t s);
+                          double *scratch, double *R_out, int64_t *iters_out, int *launches,
+                          cudaStream_t s, CgGraph *cache = nullptr);
+// one edge insert / delete of the device CSR, rows kept sorted (k9_graph_edit.cu)
+cudaError_t launch_csr_edit(int64_t n, int64_t twom, int64_t *row_off, int32_t *col,
+                            int32_t *scratch, int64_t *pos, int32_t u, int32_t v, bool insert,
+                            cudaStream_t s);
 
 // Result layout of launch_pool_reduce in `scratch`.
 struct PoolSums {

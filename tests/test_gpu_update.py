@@ -147,3 +147,94 @@ def test_cg_resistance_matches_exact(gname):
         st = G.stats()
         assert st["last_resistance"] == pytest.approx(want, rel=1e-9)
         assert st["last_cg_iters"] > 0
+
+
+def _tau0_edge_deletable(g, p0, rng):
+    """A tau0 edge (x, p0[x]) whose deletion keeps the graph connected."""
+    xs = rng.permutation(np.flatnonzero(p0 >= 0))
+    edges = {(int(a), int(b)) for a, b in g.edges()}
+    for x in xs[:200]:
+        a, b = sorted((int(x), int(p0[x])))
+        arr = np.array(sorted(edges - {(a, b)}))
+        h = S.csr_from_edges(g.n, arr[:, 0], arr[:, 1])
+        if h.n == g.n and np.all(h.deg > 0) and S.is_connected(h):
+            return a, b
+    raise RuntimeError("no deletable tau0 edge")
+
+
+@pytest.mark.parametrize("mode", [kc.KC_UPDATE_BSM, kc.KC_UPDATE_ISM])
+def test_updates_bit_exact_on_a_large_power_law_graph(mode):
+    """The device-resident update path (CSR edited on the device per op) on a
+    Chung-Lu graph of about 10^5 vertices: a mixed stream of insertions and
+    deletions, one of them an edge of tau0 (tau0 rebuilt, every f refreshed),
+    every pool value and parent array bit for bit with the oracle after each
+    op.  Deep subtrees and the crossing-count kernels meet sizes far beyond the
+    small graphs above."""
+    g = S.chung_lu(100000, 2.1, 8.0, 21)
+    seed, T = 23, 16
+    D = DynamicOracle(g, seed, T)
+    cfg = kc.kc_config_default()
+    cfg.keep_trees = 1
+    cfg.r_source = kc.KC_R_GIVEN
+    rng = np.random.default_rng(7 + mode)
+    a0, b0 = _tau0_edge_deletable(g, D.t0.p0, rng)
+    arr = np.array(sorted({(int(a), int(b)) for a, b in g.edges()} - {(a0, b0)}))
+    g2 = S.csr_from_edges(g.n, arr[:, 0], arr[:, 1])
+    ops = _ops(g2, rng, 9)
+    ops.insert(0, (a0, b0, 1))  # first: an edge of tau0 (ops after it are valid on G - e)
+    with kc.KemenyGraph.from_graph(g, cfg) as G:
+        G.sample(seed, T)
+        _compare(G, D, g.n)
+        for (a, b, op) in ops:
+            if op == 0:
+                arr = np.array(sorted(D.edges | {(a, b)}))
+                h = S.csr_from_edges(g.n, arr[:, 0], arr[:, 1])
+                R = O.resistance_sparse(h, a, b)
+                D.insert(a, b, mode, R=R)
+                G.update([(a, b, 0, R)], mode)
+            else:
+                D.delete(a, b, mode)
+                G.update([(a, b, 1)], mode)
+            _compare(G, D, g.n)
+        tau = G.tau0()
+        assert np.array_equal(tau["p0"], D.t0.p0)  # rebuilt after the tau0 deletion
+        assert G.stats()["updates_applied"] == len(ops)
+        assert G.stats()["m"] == len(D.edges)
+
+
+def test_batched_updates_equal_one_at_a_time():
+    """A batch of ops in one kc_update call gives the pool, graph and tau0 that
+    the same ops give one call at a time (the host copy of the CSR is refreshed
+    once per batch, the device copy per op)."""
+    g = S.chung_lu(20000, 2.1, 8.0, 5)
+    rng = np.random.default_rng(3)
+    ops = _ops(g, rng, 8)
+    cfg = kc.kc_config_default()
+    cfg.keep_trees = 1
+    cfg.r_source = kc.KC_R_GIVEN
+    Rs = {}
+    edges = {(int(a), int(b)) for a, b in g.edges()}
+    for (a, b, op) in ops:
+        if op == 0:
+            edges.add((a, b))
+            arr = np.array(sorted(edges))
+            Rs[(a, b)] = O.resistance_sparse(S.csr_from_edges(g.n, arr[:, 0], arr[:, 1]), a, b)
+        else:
+            edges.discard((a, b))
+    full = [(a, b, 0, Rs[(a, b)]) if op == 0 else (a, b, 1) for (a, b, op) in ops]
+    outs = []
+    for batched in (True, False):
+        with kc.KemenyGraph.from_graph(g, cfg) as G:
+            G.sample(9, 24)
+            if batched:
+                G.update(full, kc.KC_UPDATE_ISM)
+            else:
+                for o in full:
+                    G.update([o], kc.KC_UPDATE_ISM)
+            outs.append((G.samples(), G.tau0(), G.stats()["m"],
+                         [G.tree(k)["parent"] for k in range(24)]))
+    (s1, t1, m1, p1), (s2, t2, m2, p2) = outs
+    assert m1 == m2 == len(edges)
+    assert np.array_equal(s1["f"], s2["f"]) and np.array_equal(s1["w"], s2["w"])
+    assert np.array_equal(t1["p0"], t2["p0"])
+    assert all(np.array_equal(a, b) for a, b in zip(p1, p2))

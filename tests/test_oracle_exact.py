@@ -194,3 +194,19 @@ def test_resistance_and_tree_count_equal_networkx():
     for u, v in [(0, 1), (2, 7), (3, 9)]:
         assert O.resistance(g, u, v) == pytest.approx(nx.resistance_distance(G, u, v), rel=1e-9)
     assert O.kirchhoff_count(g) == pytest.approx(float(nx.number_of_spanning_trees(G)), rel=1e-9)
+
+
+@pytest.mark.parametrize("seed", [1, 2])
+def test_sparse_resistance_matches_dense_and_series_rule(seed):
+    """The sparse CG resistance equals the dense grounded inverse on random
+    graphs (both orientations, pairs at any distance), and on a path graph it
+    is the hop distance (resistors in series)."""
+    g = S.random_connected(40, 0.12, seed)
+    rng = np.random.default_rng(seed)
+    for _ in range(6):
+        u, v = (int(x) for x in rng.choice(g.n, 2, replace=False))
+        d = O.resistance(g, u, v)
+        assert O.resistance_sparse(g, u, v) == pytest.approx(d, rel=1e-10)
+        assert O.resistance_sparse(g, v, u) == pytest.approx(d, rel=1e-10)
+    p = S.path(30)
+    assert O.resistance_sparse(p, 3, 17) == pytest.approx(14.0, rel=1e-10)
