@@ -614,8 +614,9 @@ def main():
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--workload", default="grid1000")
     ap.add_argument("--trees", type=int, default=10000)
-    ap.add_argument("--warmup-trees", type=int, default=16,
-                    help="trees per warm-up step (0: same as --trees)")
+    ap.add_argument("--warmup-trees", type=int, default=-1,
+                    help="trees per warm-up step (0: same as --trees; default 16, or --trees "
+                         "with rejection, whose wave sizes learn the acceptance rate)")
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--eps", type=float, default=0.01)
     ap.add_argument("--delta", type=float, default=0.05)
@@ -672,6 +673,8 @@ def main():
     g = S.workload(args.workload)
     n = g.n
     T = args.trees
+    if args.warmup_trees < 0:
+        args.warmup_trees = 0 if args.reject_quantile > 0 else 16
     WT = args.warmup_trees or T
     from paper_2511_16356_gb300.dist import rank_sample_base
 
@@ -750,6 +753,7 @@ def main():
         dict(reject, trees_rejected=int(st["trees_rejected"] - rej0),
              note="trees/s counts accepted trees; the roofline counts their steps only"),
         "steps_per_tree": steps_total / trees_timed,
+        "step_ms": [round(x, 1) for x in step_ms],
         "gpu_launches": int(launches),
         "clocks": clk,
     }

@@ -153,9 +153,9 @@ typedef struct {
                                    the first accepted ids (not consecutive).  The
                                    tree is independent of its step count, so the
                                    accepted trees stay uniform.  At least n - 1 (each
-                                   non-root vertex departs once); needs the 32-walker
-                                   kernel, keep_trees = 0 and no autotune; not for
-                                   kc_sample_multi.  0: off (default)               */
+                                   non-root vertex departs once); needs the LANE or
+                                   WARP walker, keep_trees = 0 and no autotune; not
+                                   for kc_sample_multi.  0: off (default)           */
 } kc_config;
 
 /* Fill *cfg with the defaults listed above. */

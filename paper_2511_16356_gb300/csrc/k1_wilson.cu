@@ -38,12 +38,17 @@ __global__ void k_wave_init(int64_t n, int64_t B, int32_t root, uint64_t *word, 
 // already finished) has reached stop_at.  It then saves the order index of its
 // next start and its order position in rs_q / rs_pos (rs_q = -1 for a
 // finished tree), and the 32-walker kernel resumes the tree from there.
+// kReject: step_cap bounds the tree's departures and a tree that exceeds it is
+// abandoned (steps = -1) instead of failing the wave -- rejection by walk
+// length.  With done_flag set, each lane publishes its finished tree to the
+// host (depth + 1, or -1 when rejected) for the pipelined traversal.
+template <bool kReject>
 __global__ void __launch_bounds__(128) k_wilson(GraphView g, WaveView w, uint64_t seed,
                                                 const int64_t *__restrict__ sids,
                                                 const int32_t *__restrict__ sorder,
                                                 int64_t step_cap, int32_t *rs_q, int32_t *rs_pos,
                                                 unsigned int *done, int64_t q_stop,
-                                                int64_t stop_at) {
+                                                int64_t stop_at, volatile int32_t *done_flag) {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= w.B) return;
     const int64_t n = g.n;
@@ -63,6 +68,7 @@ __global__ void __launch_bounds__(128) k_wilson(GraphView g, WaveView w, uint64_
     int32_t len = 0, i = 0, dh = 0, maxd = 0;
     int phase = kSeek;
     bool stopped = false;
+    bool rejected = false;
 
     // Every iteration: phase-specific arithmetic, then ONE gather (the word of
     // one vertex, with its record when the lane may walk from it), then
@@ -85,7 +91,11 @@ __global__ void __launch_bounds__(128) k_wilson(GraphView g, WaveView w, uint64_
                 v = g.col[off + k];
             }
             word[u] = w_make(v, w_count(wu) + 1, false);
-            if (++steps > step_cap || w_count(wu) + 1 >= (1u << 25)) {
+            if (kReject && ++steps > step_cap) {
+                rejected = true;
+                break;
+            }
+            if ((!kReject && ++steps > step_cap) || w_count(wu) + 1 >= (1u << 25)) {
                 atomicOr(w.err, kErrStepLimit);
                 break;
             }
@@ -157,12 +167,25 @@ __global__ void __launch_bounds__(128) k_wilson(GraphView g, WaveView w, uint64_
             }
         }
     }
+    if (kReject && rejected) {
+        w.steps[t] = -1;
+        if (done_flag) {
+            __threadfence_system();
+            done_flag[t] = -1;  // finished, rejected
+        }
+        return;
+    }
     w.steps[t] = steps;
     atomicMax(w.maxdepth, maxd);
     if (rs_q) {
         rs_q[t] = stopped ? q : -1;
         rs_pos[t] = pos;
         if (!stopped) atomicAdd(done, 1u);
+    }
+    if (done_flag) {
+        // publish the finished tree (its depth + 1) after its words and order
+        __threadfence_system();
+        done_flag[t] = maxd + 1;
     }
 }
 
@@ -607,9 +630,18 @@ cudaError_t launch_wave_init(const GraphView &g, WaveView w, cudaStream_t s) {
 
 cudaError_t launch_wilson(const GraphView &g, WaveView w, uint64_t seed, const int64_t *sids,
                           int64_t step_cap, cudaStream_t s, const int32_t *sorder, int32_t *rs_q,
-                          int32_t *rs_pos, unsigned int *done, int64_t q_stop, int64_t stop_at) {
-    k_wilson<<<(unsigned)((w.B + 127) / 128), 128, 0, s>>>(g, w, seed, sids, sorder, step_cap,
-                                                           rs_q, rs_pos, done, q_stop, stop_at);
+                          int32_t *rs_pos, unsigned int *done, int64_t q_stop, int64_t stop_at,
+                          int32_t *done_flag) {
+    k_wilson<false><<<(unsigned)((w.B + 127) / 128), 128, 0, s>>>(
+        g, w, seed, sids, sorder, step_cap, rs_q, rs_pos, done, q_stop, stop_at, done_flag);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_wilson_reject(const GraphView &g, WaveView w, uint64_t seed,
+                                 const int64_t *sids, const int32_t *sorder, int64_t tree_cap,
+                                 cudaStream_t s, int32_t *done_flag) {
+    k_wilson<true><<<(unsigned)((w.B + 127) / 128), 128, 0, s>>>(
+        g, w, seed, sids, sorder, tree_cap, nullptr, nullptr, nullptr, 0, 0, done_flag);
     return cudaGetLastError();
 }
 

@@ -334,12 +334,20 @@ void run_wave_pipelined(kc_graph *g, Plan &p, int64_t B, int64_t sid0, bool reje
     KC_CK(g, cudaEventRecord(ev_ready, s1));
     KC_CK(g, cudaStreamWaitEvent(s2, ev_ready, 0));
     KC_CK(g, cudaEventRecord(ev_w0, s1));
-    if (reject)
+    if (g->walker == KC_WALK_LANE) {
+        if (reject)
+            KC_CK(g, launch_wilson_reject(gv, w, g->seed, c.sids, nullptr, g->cfg.reject_steps,
+                                          s1, g->d_done));
+        else
+            KC_CK(g, launch_wilson(gv, w, g->seed, c.sids, step_cap_of(g), s1, nullptr, nullptr,
+                                   nullptr, nullptr, 0, 0, g->d_done));
+    } else if (reject) {
         KC_CK(g, launch_wilson_warp_reject(gv, w, g->seed, c.sids, g->d_sorder,
                                            g->cfg.reject_steps, s1, g->d_done));
-    else
+    } else {
         KC_CK(g, launch_wilson_warp(gv, w, g->seed, c.sids, g->d_sorder, step_cap_of(g), s1,
                                     nullptr, nullptr, g->d_done));
+    }
     KC_CK(g, cudaEventRecord(ev_w1, s1));
     const int64_t chunk_min = std::max<int64_t>(1, std::min<int64_t>(p.BT, (B + 1) / 2));
     std::vector<int32_t> unseen((size_t)B), ready;
@@ -436,7 +444,8 @@ void run_wave_pipelined(kc_graph *g, Plan &p, int64_t B, int64_t sid0, bool reje
 void run_wave(kc_graph *g, Plan &p, int64_t B, int64_t sid0, bool canonical = false) {
     // pipelining pays when traversal and TTF take long enough to hide: several
     // sub-waves, or large graphs; short waves of small graphs run straight
-    if (!canonical && !g->tuning && g->walker == KC_WALK_WARP && B > 1 &&
+    if (!canonical && !g->tuning && (g->walker == KC_WALK_WARP || g->walker == KC_WALK_LANE) &&
+        B > 1 &&
         (B > p.BT || g->n >= (1 << 16))) {
         try {
             run_wave_pipelined(g, p, B, sid0);
@@ -1147,8 +1156,12 @@ void run_wave_reject(kc_graph *g, Plan &p, int64_t B, int64_t sid0) {
     }
     {
         Phase ph(g, g->t_wilson);
-        KC_CK(g, launch_wilson_warp_reject(gv, w, g->seed, c.sids, g->d_sorder,
-                                           g->cfg.reject_steps, g->stream));
+        if (g->walker == KC_WALK_LANE)
+            KC_CK(g, launch_wilson_reject(gv, w, g->seed, c.sids, nullptr, g->cfg.reject_steps,
+                                          g->stream));
+        else
+            KC_CK(g, launch_wilson_warp_reject(gv, w, g->seed, c.sids, g->d_sorder,
+                                               g->cfg.reject_steps, g->stream));
         ph.done(1);
     }
     uint32_t hdr[2] = {0, 0};
@@ -1666,7 +1679,7 @@ kc_status kc_graph_create(int64_t n, const int64_t *row_off, const int32_t *col,
     if (cfg.reject_steps < 0 ||
         (cfg.reject_steps > 0 &&
          (cfg.reject_steps < n - 1 || cfg.keep_trees || cfg.autotune ||
-          (cfg.walker != KC_WALK_AUTO && cfg.walker != KC_WALK_WARP))))
+          cfg.walker == KC_WALK_HYBRID)))
         return KC_ERR_INVALID_ARG;
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {

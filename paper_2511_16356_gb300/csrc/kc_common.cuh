@@ -349,7 +349,13 @@ cudaError_t launch_ttf_bit_multi(const MultiSub &ms, cudaStream_t s);
 cudaError_t launch_wilson(const GraphView &g, WaveView w, uint64_t seed, const int64_t *sids,
                           int64_t step_cap, cudaStream_t s, const int32_t *sorder = nullptr,
                           int32_t *rs_q = nullptr, int32_t *rs_pos = nullptr,
-                          unsigned int *done = nullptr, int64_t q_stop = 0, int64_t stop_at = 0);
+                          unsigned int *done = nullptr, int64_t q_stop = 0, int64_t stop_at = 0,
+                          int32_t *done_flag = nullptr);
+// one walker per tree with rejection by walk length (tree_cap departures): a
+// rejected tree gets steps = -1 (and done flag -1) and no depth or order
+cudaError_t launch_wilson_reject(const GraphView &g, WaveView w, uint64_t seed,
+                                 const int64_t *sids, const int32_t *sorder, int64_t tree_cap,
+                                 cudaStream_t s, int32_t *done_flag = nullptr);
 cudaError_t launch_wilson_warp(const GraphView &g, WaveView w, uint64_t seed, const int64_t *sids,
                                const int32_t *sorder, int64_t step_cap, cudaStream_t s,
                                const int32_t *rs_q = nullptr, const int32_t *rs_pos = nullptr,

@@ -214,19 +214,29 @@ def test_hoeffding_rule_draws_theorem5_trees(name, eps):
     assert k == pytest.approx(O.estimate_fixed(f, 2 * g.m), rel=1e-12)
 
 
+@pytest.mark.parametrize("walker", ["warp", "lane"])
 @pytest.mark.parametrize("name,trees", [("grid17x13", 500), ("er300", 500), ("cl3000", 500),
-                                        ("cl80000", 96)])
-def test_rejection_by_walk_length_matches_oracle(name, trees):
+                                        ("cl80000", 96), ("grid300x300", 24)])
+def test_rejection_by_walk_length_matches_oracle(name, trees, walker):
     """With reject_steps = X the pool holds the first sample ids whose Wilson
     step count is at most X, with the oracle's f and step counts (the oracle's
     accepted_samples); the other ids drawn are counted as rejected.  The
-    80000-vertex graph takes the pipelined waves, the others the plain ones."""
-    g = S.chung_lu(80000, 2.1, 10.0, 6) if name == "cl80000" else SMALL[name]()
+    80000-vertex graph and the 300x300 grid (BIT variant) take the pipelined
+    waves, the others the plain ones; both walkers."""
+    if name == "cl80000":
+        g = S.chung_lu(80000, 2.1, 10.0, 6)
+    elif name == "grid300x300":
+        g = S.workload("grid300x300")
+    else:
+        g = SMALL[name]()
     t0 = O.tau0(g)
-    _, s_all = O.sample_batch(g, t0, 5, 0, 8 * trees)
+    probe = 4 * trees if name == "grid300x300" else 8 * trees  # oracle trees of the big grid are slow
+    _, s_all = O.sample_batch(g, t0, 5, 0, probe)
     cap = int(np.quantile(s_all, 0.7))
-    ids, f, steps = O.accepted_samples(lambda a, c: O.sample_batch(g, t0, 5, a, c), cap, trees)
-    with kc.KemenyGraph.from_graph(g, _cfg(keep_trees=0, reject_steps=cap)) as G:
+    ids, f, steps = O.accepted_samples(lambda a, c: O.sample_batch(g, t0, 5, a, c), cap, trees,
+                                       block=2 * trees)
+    wk = kc.KC_WALK_WARP if walker == "warp" else kc.KC_WALK_LANE
+    with kc.KemenyGraph.from_graph(g, _cfg(keep_trees=0, reject_steps=cap, walker=wk)) as G:
         G.sample(5, trees)
         got = G.samples()
         assert np.array_equal(got["sid"], ids)
