@@ -452,10 +452,34 @@ def batched_leg(args, kc):
 def update_stream(g, n_updates: int, bmax: int, seed: int = 4):
     """Seeded edge-update batches against the evolving graph: half insertions of
     absent pairs, half deletions of edges that lie on a triangle (never a
-    bridge), batch sizes uniform on [1, bmax]."""
+    bridge), batch sizes uniform on [1, bmax].  The first k ops of a longer
+    stream are the stream of length k (only the last batch is cut short).  The
+    evolving graph is the CSR plus small sets of added and removed edges, so a
+    prefix of a stream on a 10^7-edge graph costs no per-vertex Python state."""
     rng = np.random.default_rng(seed)
-    adj = [set(g.col[g.row_off[v]:g.row_off[v + 1]].tolist()) for v in range(g.n)]
-    edges = [tuple(e) for e in g.edges().tolist()]
+    ro, col = g.row_off, g.col
+    added, removed = set(), set()
+    extra = {}  # vertex -> neighbours added by the stream
+
+    def key(u, v):
+        return (u, v) if u < v else (v, u)
+
+    def has(u, v):
+        k = key(u, v)
+        if k in added:
+            return True
+        if k in removed:
+            return False
+        a, b = ro[u], ro[u + 1]
+        i = a + int(np.searchsorted(col[a:b], v))
+        return i < b and int(col[i]) == v
+
+    def nbrs(u):
+        base = col[ro[u]:ro[u + 1]].tolist()
+        out = {x for x in base if key(u, x) not in removed}
+        return out | extra.get(u, set())
+
+    added_list = []
     batches, done = [], 0
     while done < n_updates:
         b = int(min(rng.integers(1, bmax + 1), n_updates - done))
@@ -463,21 +487,34 @@ def update_stream(g, n_updates: int, bmax: int, seed: int = 4):
         while len(ops) < b:
             if rng.random() < 0.5:
                 u, v = (int(x) for x in rng.choice(g.n, 2, replace=False))
-                if v in adj[u]:
+                if has(u, v):
                     continue
-                adj[u].add(v)
-                adj[v].add(u)
-                edges.append((min(u, v), max(u, v)))
+                k = key(u, v)
+                if k in removed:
+                    removed.discard(k)
+                else:
+                    added.add(k)
+                    added_list.append(k)
+                extra.setdefault(u, set()).add(v)
+                extra.setdefault(v, set()).add(u)
                 ops.append((u, v, 0))
             else:
-                k = int(rng.integers(len(edges)))
-                u, v = edges[k]
-                if v not in adj[u] or not (adj[u] & adj[v]):
+                e = int(rng.integers(len(col) // 2 + len(added_list)))
+                if e < len(col) // 2:  # the e-th edge (u < v) of the base graph
+                    x = int(rng.integers(len(col)))
+                    u = int(np.searchsorted(ro, x, side="right") - 1)
+                    v = int(col[x])
+                else:
+                    u, v = added_list[e - len(col) // 2]
+                if not has(u, v) or not (nbrs(u) & nbrs(v)):
                     continue
-                adj[u].discard(v)
-                adj[v].discard(u)
-                edges[k] = edges[-1]
-                edges.pop()
+                k = key(u, v)
+                if k in added:
+                    added.discard(k)
+                else:
+                    removed.add(k)
+                extra.get(u, set()).discard(v)
+                extra.get(v, set()).discard(u)
                 ops.append((u, v, 1))
         batches.append(ops)
         done += b
@@ -485,38 +522,74 @@ def update_stream(g, n_updates: int, bmax: int, seed: int = 4):
 
 
 def dynamic_leg(args, kc):
-    """Sample maintenance under a stream of update batches with a Kemeny query
-    after each batch: ISM against BSM on the same pool and stream."""
+    """Dynamic serving at its stated size: a Chung-Lu graph (gamma 2.1, mean
+    degree 20), a pool of `--dyn-trees` retained trees maintained on the device,
+    and the first `--dyn-updates` ops of the seeded update stream (batches
+    uniform on 1..`--dyn-batch`; only a prefix fits a bench run), with a Kemeny
+    query at eps after each batch.  ISM (Algorithm 3) against BSM (Algorithm 2)
+    on the same pool and ops; R(u, v) by device CG.  K error: the maintained
+    estimates against a fresh pool of the same size drawn on the final graph."""
+    import torch
+
     from paper_2511_16356_gb300 import synth as S
 
     g = S.chung_lu(args.dyn_n, 2.1, 20.0, 4)
+    t = time.perf_counter()
     batches = update_stream(g, args.dyn_updates, args.dyn_batch)
+    gen_s = time.perf_counter() - t
     out = {"workload": f"Chung-Lu gamma 2.1, mean degree 20, seed 4 (n = {g.n:,}, m = {g.m:,}); "
-                       f"{args.dyn_updates} updates in {len(batches)} batches of 1-"
-                       f"{args.dyn_batch}, half insertions, half deletions of triangle edges; "
-                       f"pool of {args.dyn_trees} trees; a query at eps {args.eps} after "
-                       f"each batch"}
+                       f"the first {args.dyn_updates} ops of the seeded update stream (batches "
+                       f"uniform on 1..{args.dyn_batch}: {len(batches)} batch(es) here), half "
+                       f"insertions of absent pairs, half deletions of edges on a triangle (never "
+                       f"a bridge); pool of {args.dyn_trees} trees; a query at eps {args.eps} "
+                       f"after each batch", "ops": args.dyn_updates, "stream_gen_s": gen_s}
+    finals = {}
     for name, mode in (("ism", kc.KC_UPDATE_ISM), ("bsm", kc.KC_UPDATE_BSM)):
         cfg = kc.kc_config_default()
         cfg.keep_trees = 1
         G = kc.KemenyGraph.from_graph(g, cfg)
+        t = time.perf_counter()
         G.sample(args.seed, args.dyn_trees)
-        upd_s, q_ms = 0.0, []
-        k_hat = 0.0
+        torch.cuda.synchronize()
+        pool_s = time.perf_counter() - t
+        k0 = G.estimate()
+        upd_ms, q_ms = [], []
+        k_hat = k0
         for ops in batches:
             t = time.perf_counter()
             G.update(ops, mode)
-            upd_s += time.perf_counter() - t
+            upd_ms.append(1000.0 * (time.perf_counter() - t) / len(ops))
             t = time.perf_counter()
             k_hat = G.estimate(args.eps, args.delta)
             q_ms.append(1000.0 * (time.perf_counter() - t))
         st = G.stats()
+        finals[name] = k_hat
         G.close()
-        out[name] = {"update_ms_per_op": 1000.0 * upd_s / max(1, args.dyn_updates),
+        ops_n = sum(len(b) for b in batches)
+        out[name] = {"update_ms_per_op": float(np.average(upd_ms, weights=[len(b) for b in batches])),
+                     "update_ms_per_op_device": st["ms_update"] / max(1, ops_n),
                      "query_p50_ms": float(np.percentile(q_ms, 50)),
                      "query_p99_ms": float(np.percentile(q_ms, 99)),
                      "trees_resampled": int(st["trees_resampled"]),
-                     "pool_trees": int(st["pool_trees"]), "K_final": k_hat}
+                     "pool_trees": int(st["pool_trees"]), "pool_build_s": pool_s,
+                     "K_before": k0, "K_after": k_hat, "last_cg_iters": int(st["last_cg_iters"])}
+    # reference: a fresh pool of the same size on the final graph
+    ins = {(min(u, v), max(u, v)) for b in batches for u, v, op in b if op == 0}
+    dele = {(min(u, v), max(u, v)) for b in batches for u, v, op in b if op == 1}
+    e = {(int(a), int(b)) for a, b in g.edges()}
+    e = (e | ins) - dele if len(ins & dele) == 0 else None
+    if e is not None:
+        arr = np.array(sorted(e))
+        g2 = S.csr_from_edges(g.n, arr[:, 0], arr[:, 1])
+        cfg = kc.kc_config_default()
+        cfg.keep_trees = 0
+        F = kc.KemenyGraph.from_graph(g2, cfg)
+        F.sample(args.seed + 1, args.dyn_trees)
+        k_ref = F.estimate()
+        F.close()
+        out["K_fresh_pool"] = k_ref
+        for name in ("ism", "bsm"):
+            out[name]["rel_diff_vs_fresh"] = (finals[name] - k_ref) / k_ref
     return out
 
 
@@ -650,10 +723,11 @@ def main():
                     help="trees of the probe batch that sets the rejection cap")
     ap.add_argument("--dynamic", action="store_true",
                     help="also run the update-stream leg (ISM against BSM)")
-    ap.add_argument("--dyn-n", type=int, default=100000)
-    ap.add_argument("--dyn-updates", type=int, default=1000)
-    ap.add_argument("--dyn-batch", type=int, default=100)
-    ap.add_argument("--dyn-trees", type=int, default=1000)
+    ap.add_argument("--dyn-n", type=int, default=1000000)
+    ap.add_argument("--dyn-updates", type=int, default=32,
+                    help="ops of the seeded update stream processed (a prefix)")
+    ap.add_argument("--dyn-batch", type=int, default=1000)
+    ap.add_argument("--dyn-trees", type=int, default=5000)
     args = ap.parse_args()
     if args.warmup < 3:
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)

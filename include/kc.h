@@ -352,6 +352,13 @@ typedef struct {
 } kc_pool_sums;
 
 /*
+ * The pool's sums (one reduction on the device, read back on the handle's
+ * stream): exact int128 sum of the unit-weight f, FP64 moments, tree count.
+ * Errors: INVALID_ARG, CUDA.  An empty pool gives all zeros.
+ */
+kc_status kc_get_pool_sums(kc_graph *g, kc_pool_sums *out);
+
+/*
  * Combine per-shard sums (host only, no device work): the int128 f sums are
  * added exactly; the FP64 sums are added in array order, so every rank that
  * combines the same gathered array gets the same bits.  Errors: INVALID_ARG

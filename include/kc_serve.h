@@ -39,6 +39,18 @@ typedef struct {
                                requests (0: half the free device memory at creation)    */
     int64_t request_bytes;  /* workspace cap of one request (0: budget / workers); a
                                request reserves min(cap, 4096 trees' worth) until done  */
+    int32_t coalesce;       /* 1: QUERY requests on graphs of at most coalesce_max_n
+                               vertices are run together by a dispatcher thread: in
+                               each round every admitted query draws its next batch of
+                               trees, and the walks of all of them share one launch
+                               (kc_sample_multi); queries join and leave between rounds.
+                               Each query draws the same trees and takes the same
+                               stopping decisions as kc_estimate, so its K is the one
+                               it gets alone.  Larger graphs, and graphs with the
+                               Hoeffding rule, rejection or the autotuner, stay with
+                               the workers.  0: off                                 */
+    int32_t reserved;
+    int64_t coalesce_max_n; /* 0: 2^18                                                */
 } kc_server_config;
 
 /* Request kinds. */

@@ -2159,6 +2159,24 @@ kc_status kc_stats(kc_graph *g, kc_stats_t *out) {
     return KC_OK;
 }
 
+kc_status kc_get_pool_sums(kc_graph *g, kc_pool_sums *out) {
+    if (!g || !out) return KC_ERR_INVALID_ARG;
+    std::memset(out, 0, sizeof(*out));
+    if (g->pool == 0) return KC_OK;
+    try {
+        const PoolSums s = reduce_pool(g);
+        out->f_sum_hi = s.f_hi;
+        out->f_sum_lo = s.f_lo;
+        out->wf_sum = s.wf;
+        out->w_sum = s.w;
+        out->x2_sum = s.x2;
+        out->count = s.count;
+    } catch (Fail &f) {
+        return f.st;
+    }
+    return KC_OK;
+}
+
 kc_status kc_combine_sums(const kc_pool_sums *parts, int32_t count, kc_pool_sums *out) {
     if (!parts || !out || count < 1) return KC_ERR_INVALID_ARG;
     __int128 f = 0;

@@ -16,6 +16,7 @@
 
 #include "../../include/kc_serve.h"
 #include "kc_host_admit.h"
+#include "kc_host_stop.h"
 
 namespace {
 
@@ -23,7 +24,20 @@ struct Graph {
     kc_graph *h = nullptr;
     int64_t n = 0;
     bool dynamic = false;  // maintained pool (POOL_QUERY / UPDATE) vs fresh pools (QUERY)
-    bool busy = false;     // a worker is running one of its requests
+    bool busy = false;     // a worker (or the dispatcher) is running one of its requests
+    bool coalesced = false;  // its QUERY requests go to the dispatcher
+    kc_config cfg{};
+};
+
+// A QUERY advanced by the dispatcher: kc_estimate's normal-approximation rule
+// (kc_host_stop.h) as a state machine, one tree batch per round.
+struct Active {
+    int64_t ticket = 0;
+    int64_t bytes = 0;
+    int64_t pool = 0;     // trees drawn so far
+    int round = -1;       // -1: the pilot batch is next; then checks 0 .. 63
+    double z = 0;
+    int64_t batch = 0, cap = 0;
 };
 
 struct Request {
@@ -46,6 +60,10 @@ struct kc_server {
     std::deque<Graph> graphs;                    // stable addresses while graphs are added
     std::vector<std::unique_ptr<Request>> reqs;  // by ticket (read under the lock)
     std::deque<int64_t> queue;                   // waiting tickets, submission order
+    std::deque<int64_t> cqueue;                  // waiting coalesced QUERY tickets
+    std::thread dispatcher;
+    cudaStream_t dstream = nullptr;
+    int64_t rounds = 0;                          // dispatcher rounds (kc_sample_multi calls)
     int64_t reserved = 0;                        // bytes reserved by running requests
     int64_t outstanding = 0;                     // submitted and not yet done
     bool stop = false;
@@ -66,8 +84,9 @@ struct kc_server {
         return want < cfg.request_bytes ? want : cfg.request_bytes;
     }
 
-    // the first waiting request that may start now (kc_host_admit.h)
-    bool pick(int64_t *ticket, int64_t *bytes) {
+    // the first waiting request of q that may start now (kc_host_admit.h)
+    bool pick(int64_t *ticket, int64_t *bytes, std::deque<int64_t> *qp = nullptr) {
+        std::deque<int64_t> &queue = qp ? *qp : this->queue;
         auto it = kc_host::first_admissible(
             queue.begin(), queue.end(), graphs.size(),
             [&](int64_t t) { return reqs[(size_t)t]->graph; },
@@ -134,6 +153,129 @@ struct kc_server {
     }
 };
 
+// The coalescing dispatcher.  Between rounds it admits waiting coalesced
+// queries (submission order per graph, within the budget), then gives every
+// admitted query its next batch: the pilot, or what the stopping rule asks
+// for after the previous batch (kc_host::clt_more on the pool's sums).  A query
+// whose rule says stop, or that has had 64 checks, takes K from its pool and
+// leaves.  The batches of one round run as one kc_sample_multi call (all
+// walks in one launch) on the dispatcher's stream.
+void dispatch_loop(kc_server *s) {
+    cudaSetDevice(s->device);
+    std::vector<Active> act;
+    for (;;) {
+        {
+            std::unique_lock<std::mutex> lk(s->mu);
+            int64_t ticket = -1, bytes = 0;
+            // sleep only when nothing runs here and nothing waiting fits
+            s->cv_work.wait(lk, [&] {
+                return s->stop || !act.empty() ||
+                       (!s->cqueue.empty() && s->pick(&ticket, &bytes, &s->cqueue));
+            });
+            for (;;) {
+                if (ticket < 0 && (s->cqueue.empty() || !s->pick(&ticket, &bytes, &s->cqueue)))
+                    break;
+                Request &r = *s->reqs[(size_t)ticket];
+                Graph &g = s->graphs[(size_t)r.graph];
+                g.busy = true;
+                s->reserved += bytes;
+                Active a;
+                a.ticket = ticket;
+                a.bytes = bytes;
+                a.z = kc_host::inv_normal_upper(r.delta / 2.0);
+                a.batch = g.cfg.batch_trees > 0 ? g.cfg.batch_trees : 1024;
+                a.cap = g.cfg.max_trees > 0 ? g.cfg.max_trees : ((int64_t)1 << 24);
+                act.push_back(a);
+                r.info.t_start_ms = s->now_ms();
+                r.info.worker = -1;
+                r.info.workspace_bytes = bytes;
+                ticket = -1;
+            }
+            if (act.empty() && s->stop) return;
+            if (act.empty()) continue;
+        }
+        // set up newly admitted queries (fresh pool under the request's seed)
+        std::vector<kc_graph *> hs;
+        std::vector<uint64_t> seeds;
+        std::vector<int64_t> ks;
+        std::vector<size_t> who;
+        std::vector<std::pair<size_t, kc_status>> finished;
+        for (size_t i = 0; i < act.size(); ++i) {
+            Active &a = act[i];
+            Request &r = *s->reqs[(size_t)a.ticket];
+            kc_graph *h = s->graphs[(size_t)r.graph].h;
+            kc_status st = KC_OK;
+            int64_t k = 0;
+            if (a.round < 0) {
+                st = kc_graph_set_stream(h, s->dstream);
+                if (st == KC_OK) st = kc_graph_set_workspace_limit(h, a.bytes - a.bytes / 8);
+                if (st == KC_OK) st = kc_graph_reset(h, r.seed, 0);
+                k = std::max<int64_t>(64, std::min(a.batch, a.cap));  // the pilot
+                a.round = 0;
+            } else if (a.round >= 64) {
+                k = 0;
+            } else {
+                kc_pool_sums ps;
+                st = kc_get_pool_sums(h, &ps);
+                if (st == KC_OK)
+                    k = kc_host::clt_more(kc_host::Moments{ps.count, ps.wf_sum, ps.w_sum, ps.x2_sum},
+                                          a.z, r.eps, a.batch, a.cap, a.pool);
+                ++a.round;
+            }
+            if (st != KC_OK || k <= 0) {
+                finished.push_back({i, st});
+                continue;
+            }
+            hs.push_back(h);
+            seeds.push_back(r.seed);
+            ks.push_back(k);
+            who.push_back(i);
+        }
+        if (!hs.empty()) {
+            const kc_status st = kc_sample_multi(hs.data(), seeds.data(), ks.data(), (int32_t)hs.size());
+            ++s->rounds;
+            for (size_t j = 0; j < who.size(); ++j) {
+                if (st != KC_OK) finished.push_back({who[j], st});
+                else act[who[j]].pool += ks[j];
+            }
+        }
+        // finish: K from the pool (the exact int128 numerator), release
+        std::vector<char> gone(act.size(), 0);
+        for (auto &fs : finished) {
+            Active &a = act[fs.first];
+            Request &r = *s->reqs[(size_t)a.ticket];
+            Graph &g = s->graphs[(size_t)r.graph];
+            kc_status st = fs.second;
+            double K = 0;
+            if (st == KC_OK) st = kc_estimate(g.h, 0.0, 0.0, &K);
+            kc_graph_release_workspace(g.h);
+            cudaStreamSynchronize(s->dstream);
+            kc_stats_t stt;
+            std::memset(&stt, 0, sizeof(stt));
+            if (kc_stats(g.h, &stt) == KC_OK) r.info.trees = stt.pool_trees;
+            r.info.status = st;
+            r.info.K = K;
+            r.info.t_end_ms = s->now_ms();
+            {
+                std::lock_guard<std::mutex> lk(s->mu);
+                g.busy = false;
+                s->reserved -= a.bytes;
+                r.done = true;
+                --s->outstanding;
+            }
+            gone[fs.first] = 1;
+        }
+        if (!finished.empty()) {
+            std::vector<Active> keep;
+            for (size_t i = 0; i < act.size(); ++i)
+                if (!gone[i]) keep.push_back(act[i]);
+            act.swap(keep);
+            s->cv_work.notify_all();
+            s->cv_done.notify_all();
+        }
+    }
+}
+
 extern "C" {
 
 void kc_server_config_default(kc_server_config *cfg) {
@@ -186,6 +328,16 @@ kc_status kc_server_create(const kc_server_config *cfg_in, kc_server **out) {
         }
         s->streams.push_back(st);
     }
+    if (cfg.coalesce) {
+        if (cfg.coalesce_max_n <= 0) cfg.coalesce_max_n = (int64_t)1 << 18;
+        s->cfg = cfg;
+        if (cudaStreamCreateWithFlags(&s->dstream, cudaStreamNonBlocking) != cudaSuccess) {
+            for (cudaStream_t x : s->streams) cudaStreamDestroy(x);
+            delete s;
+            return KC_ERR_CUDA;
+        }
+        s->dispatcher = std::thread([s] { dispatch_loop(s); });
+    }
     for (int i = 0; i < cfg.workers; ++i) s->workers.emplace_back([s, i] { s->run(i); });
     *out = s;
     return KC_OK;
@@ -207,8 +359,10 @@ kc_status kc_server_destroy(kc_server *s) {
     }
     s->cv_work.notify_all();
     for (auto &t : s->workers) t.join();
+    if (s->dispatcher.joinable()) s->dispatcher.join();
     for (auto &g : s->graphs) kc_graph_destroy(g.h);
     for (cudaStream_t x : s->streams) cudaStreamDestroy(x);
+    if (s->dstream) cudaStreamDestroy(s->dstream);
     delete s;
     return KC_OK;
 }
@@ -240,6 +394,9 @@ kc_status kc_server_add_graph(kc_server *s, int64_t n, const int64_t *row_off, c
     g.h = h;
     g.n = n;
     g.dynamic = pool_trees > 0;
+    g.cfg = cfg;
+    g.coalesced = s->cfg.coalesce && !g.dynamic && n <= s->cfg.coalesce_max_n &&
+                  cfg.stop_rule == KC_STOP_CLT && cfg.reject_steps == 0 && !cfg.autotune;
     s->graphs.push_back(g);
     *graph_id = (int32_t)(s->graphs.size() - 1);
     return KC_OK;
@@ -253,8 +410,9 @@ static kc_status submit(kc_server *s, std::unique_ptr<Request> r, int64_t *ticke
         r->info.worker = -1;
         r->info.t_submit_ms = s->now_ms();
         const int64_t t = (int64_t)s->reqs.size();
+        const bool co = r->kind == KC_REQ_QUERY && s->graphs[(size_t)r->graph].coalesced;
         s->reqs.push_back(std::move(r));
-        s->queue.push_back(t);
+        (co ? s->cqueue : s->queue).push_back(t);
         ++s->outstanding;
         *ticket = t;
     }

@@ -94,7 +94,9 @@ class kc_pool_sums(ctypes.Structure):
 
 class kc_server_config(ctypes.Structure):
     _fields_ = [("struct_size", ctypes.c_uint32), ("workers", ctypes.c_int32),
-                ("budget_bytes", ctypes.c_int64), ("request_bytes", ctypes.c_int64)]
+                ("budget_bytes", ctypes.c_int64), ("request_bytes", ctypes.c_int64),
+                ("coalesce", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("coalesce_max_n", ctypes.c_int64)]
 
 
 class kc_request_info(ctypes.Structure):
@@ -135,6 +137,7 @@ _SIGS = {
                                          _P, _P]),
     "kc_stats": (ctypes.c_int, [_P, ctypes.POINTER(kc_stats_t)]),
     "kc_reset_timers": (ctypes.c_int, [_P]),
+    "kc_get_pool_sums": (ctypes.c_int, [_P, ctypes.POINTER(kc_pool_sums)]),
     "kc_combine_sums": (ctypes.c_int, [ctypes.POINTER(kc_pool_sums), ctypes.c_int32,
                                        ctypes.POINTER(kc_pool_sums)]),
     "kc_estimate_from_sums": (ctypes.c_int, [ctypes.POINTER(kc_pool_sums), ctypes.c_int64,
@@ -375,6 +378,11 @@ class KemenyGraph:
     def stats(self) -> dict:
         return kc_stats(self.h)
 
+    def pool_sums(self) -> dict:
+        s = kc_pool_sums()
+        _check(load().kc_get_pool_sums(self.h, ctypes.byref(s)), "kc_get_pool_sums", self.h)
+        return {k: getattr(s, k) for k, _ in s._fields_}
+
     def close(self):
         if getattr(self, "h", None):
             kc_graph_destroy(self.h)
@@ -405,10 +413,12 @@ def _edge_ops(ops):
 class Server:
     """Owning wrapper around a kc_server (resident graphs, continuous batching)."""
 
-    def __init__(self, workers: int = 4, budget_bytes: int = 0, request_bytes: int = 0):
+    def __init__(self, workers: int = 4, budget_bytes: int = 0, request_bytes: int = 0,
+                 coalesce: int = 0, coalesce_max_n: int = 0):
         c = kc_server_config()
         load().kc_server_config_default(ctypes.byref(c))
         c.workers, c.budget_bytes, c.request_bytes = workers, budget_bytes, request_bytes
+        c.coalesce, c.coalesce_max_n = coalesce, coalesce_max_n
         self.h = _P()
         _check(load().kc_server_create(ctypes.byref(c), ctypes.byref(self.h)), "kc_server_create")
 

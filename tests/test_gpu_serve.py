@@ -146,3 +146,32 @@ def test_request_errors_are_reported():
         assert kc.STATUS[info["status"]] == "KC_ERR_EDGE_EXISTS"
         # the graph still serves
         assert srv.wait(srv.pool_query(did, 0.05, 0.05))["status"] == kc.KC_OK
+
+
+@pytest.mark.parametrize("max_n", [0, 4000])
+def test_coalesced_queries_same_as_alone(max_n):
+    """With coalescing, queries on small graphs advance together (one
+    kc_sample_multi launch per round) and still return exactly the K and tree
+    count they get alone; with coalesce_max_n = 4000 the larger graphs stay
+    with the workers while the small ones are coalesced, in the same mix."""
+    gs = _graphs()
+    alone = []
+    with kc.Server(workers=1) as srv:
+        ids = [srv.add_graph(g, _static_cfg()) for g in gs]
+        for gi, seed, eps, delta in QUERIES:
+            info = srv.wait(srv.query(ids[gi], seed, eps, delta))
+            alone.append((info["K"], info["trees"]))
+    with kc.Server(workers=2, coalesce=1, coalesce_max_n=max_n) as srv:
+        ids = [srv.add_graph(g, _static_cfg()) for g in gs]
+        tickets = [srv.query(ids[gi], seed, eps, delta) for gi, seed, eps, delta in QUERIES * 2]
+        srv.drain()
+        infos = [srv.wait(t) for t in tickets]
+    limit = max_n or (1 << 18)
+    for k, info in enumerate(infos):
+        gi = QUERIES[k % len(QUERIES)][0]
+        assert info["status"] == kc.KC_OK
+        assert (info["K"], info["trees"]) == alone[k % len(QUERIES)]
+        if gs[gi].n <= limit:
+            assert info["worker"] == -1  # run by the dispatcher
+        else:
+            assert info["worker"] >= 0
