@@ -395,30 +395,39 @@ def other_workload_leg(args, kc, stream, flush, name: str, T: int, steps: int, w
 
 
 
-def serve_workload(n_graphs: int, n_max: int, seed: int = 3):
-    """Mixed resident graphs: ER, perturbed grids and Chung-Lu graphs with n
-    log-uniform on [1e3, n_max] (seeded)."""
+def _serve_graph(spec):
+    """One graph of the serving mix (module level, so a spawned pool can run it)."""
     from paper_2511_16356_gb300 import synth as S
 
+    kind, n, seed = spec
+    if kind == 0:
+        return S.er_lcc(n, 8.0 / n, seed)
+    if kind == 1:
+        w = max(8, int(np.sqrt(n)))
+        return S.grid_perturbed(w, max(8, n // w), 0.25, seed)
+    return S.chung_lu(n, 2.1, 10.0, seed)
+
+
+def serve_workload(n_graphs: int, n_max: float, seed: int = 3, procs: int = 0):
+    """Mixed resident graphs: ER, perturbed grids and Chung-Lu graphs in turn,
+    with n log-uniform on [1e3, n_max] (seeded).  procs > 1 generates them in a
+    pool of spawned processes (spawn: the parent may already hold a CUDA
+    context, which a forked child must not inherit)."""
     rng = np.random.default_rng(seed)
-    gs = []
-    for i in range(n_graphs):
-        n = int(np.exp(rng.uniform(np.log(1e3), np.log(n_max))))
-        kind = i % 3
-        if kind == 0:
-            gs.append(S.er_lcc(n, 8.0 / n, 100 + i))
-        elif kind == 1:
-            w = max(8, int(np.sqrt(n)))
-            gs.append(S.grid_perturbed(w, max(8, n // w), 0.25, 100 + i))
-        else:
-            gs.append(S.chung_lu(n, 2.1, 10.0, 100 + i))
-    return gs
+    specs = [(i % 3, int(np.exp(rng.uniform(np.log(1e3), np.log(n_max)))), 100 + i)
+             for i in range(n_graphs)]
+    if procs > 1:
+        import multiprocessing as mp
+
+        with mp.get_context("spawn").Pool(procs) as pool:
+            return pool.map(_serve_graph, specs, chunksize=1)
+    return [_serve_graph(sp) for sp in specs]
 
 
 def batched_leg(args, kc):
     """Many small graphs: one kc_sample_multi call (all walks in one launch)
     against one kc_sample call per graph, same trees."""
-    gs = serve_workload(args.serve_graphs, args.serve_nmax)
+    gs = serve_workload(args.batched_graphs, args.batched_nmax)
     T = args.batched_trees
     cfg = kc.kc_config_default()
     cfg.keep_trees = 0
@@ -444,7 +453,8 @@ def batched_leg(args, kc):
 
     v_b, f_b = run(True)
     v_s, f_s = run(False)
-    return {"workload": f"{len(gs)} graphs of the serving mix, {T} trees each",
+    return {"workload": f"{len(gs)} graphs of the serving mix with n log-uniform on [1e3, "
+                        f"{args.batched_nmax:.0e}], {T} trees each",
             "batched_trees_per_s": v_b, "separate_calls_trees_per_s": v_s,
             "identical_results": all(np.array_equal(a, b) for a, b in zip(f_b, f_s))}
 
@@ -594,9 +604,18 @@ def dynamic_leg(args, kc):
 
 
 def serve_leg(args, kc):
-    """Served (continuous batching, `--serve-workers` streams) against the plain
-    one-graph-per-call path on the same Poisson stream of Kemeny queries."""
-    gs = serve_workload(args.serve_graphs, args.serve_nmax)
+    """Served (continuous batching on `--serve-workers` streams, small-graph
+    queries coalesced into one launch per round) against the plain
+    one-graph-per-call path on the same Poisson streams of Kemeny queries, at
+    each offered load of `--serve-loads` (multiples of the plain path's closed-
+    loop capacity: below 1 the plain path keeps up, above it queues).  Both
+    paths give every request the same workspace cap; every K must agree."""
+    import torch
+
+    t = time.perf_counter()
+    gs = serve_workload(args.serve_graphs, args.serve_nmax,
+                        procs=min(host_cores(), 16) if args.serve_graphs > 64 else 0)
+    gen_s = time.perf_counter() - t
     rng = np.random.default_rng(7)
     Q = args.serve_queries
     q_graph = rng.integers(0, len(gs), size=Q)
@@ -605,42 +624,57 @@ def serve_leg(args, kc):
     delta = 0.05
     cfg = kc.kc_config_default()
     cfg.keep_trees = 0
+    free, _ = torch.cuda.mem_get_info()
+    budget = int(free * 0.5)
+    per_req = budget // args.serve_workers
     handles = [kc.KemenyGraph.from_graph(g, cfg) for g in gs]
+    resident = sum(int(g.row_off.nbytes + g.col.nbytes) + 52 * g.n for g in gs)
 
     def plain_one(i):
         G = handles[int(q_graph[i])]
+        kc.kc_graph_set_workspace_limit(G.h, per_req - per_req // 8)
         G.reset(int(q_seed[i]))
-        return G.estimate(float(q_eps[i]), delta)
+        k = G.estimate(float(q_eps[i]), delta)
+        kc.kc_graph_release_workspace(G.h)
+        return k
 
     for i in range(min(8, Q)):  # warm-up
         plain_one(i)
+    torch.cuda.synchronize()
     t = time.perf_counter()
     for i in range(Q):
         plain_one(i)
+    torch.cuda.synchronize()
     closed = time.perf_counter() - t
-    rate = args.serve_load * Q / closed  # offered load: a multiple of the plain capacity
-    arrivals = np.cumsum(rng.exponential(1.0 / rate, size=Q))
+    capacity = Q / closed
 
-    # plain: one query at a time in arrival order (latency includes queueing)
-    lat_p, k_p = [], []
-    t0 = time.perf_counter()
-    for i in range(Q):
-        now = time.perf_counter() - t0
-        if now < arrivals[i]:
-            time.sleep(arrivals[i] - now)
-        k_p.append(plain_one(i))
-        lat_p.append(time.perf_counter() - t0 - arrivals[i])
-    span_p = time.perf_counter() - t0
-    for G in handles:
-        G.close()
+    def summ(lat, span):
+        a = np.asarray(lat) * 1000.0
+        return {"p50_ms": float(np.percentile(a, 50)), "p99_ms": float(np.percentile(a, 99)),
+                "qps": Q / span}
 
-    # served: submit at arrival, workers overlap requests on the device
-    lat_s, k_s = [], []
-    with kc.Server(workers=args.serve_workers) as srv:
-        ids = [srv.add_graph(g, cfg) for g in gs]
-        for i in range(min(8, Q)):  # warm-up
-            srv.wait(srv.query(ids[int(q_graph[i])], int(q_seed[i]), float(q_eps[i]), delta))
-        tickets = []
+    loads = {}
+    identical = True
+    srv = kc.Server(workers=args.serve_workers, budget_bytes=budget, request_bytes=per_req,
+                    coalesce=1)
+    ids = [srv.add_graph(g, cfg) for g in gs]
+    for i in range(min(8, Q)):  # warm-up
+        srv.wait(srv.query(ids[int(q_graph[i])], int(q_seed[i]), float(q_eps[i]), delta))
+    for load in args.serve_loads:
+        rate = load * capacity
+        arrivals = np.cumsum(rng.exponential(1.0 / rate, size=Q))
+        # plain: one query at a time in arrival order (latency includes queueing)
+        lat_p, k_p = [], []
+        t0 = time.perf_counter()
+        for i in range(Q):
+            now = time.perf_counter() - t0
+            if now < arrivals[i]:
+                time.sleep(arrivals[i] - now)
+            k_p.append(plain_one(i))
+            lat_p.append(time.perf_counter() - t0 - arrivals[i])
+        span_p = time.perf_counter() - t0
+        # served: submit at arrival, requests overlap on the device
+        lat_s, k_s, tickets = [], [], []
         t0 = time.perf_counter()
         for i in range(Q):
             now = time.perf_counter() - t0
@@ -649,26 +683,31 @@ def serve_leg(args, kc):
             tickets.append((time.perf_counter() - t0,
                             srv.query(ids[int(q_graph[i])], int(q_seed[i]), float(q_eps[i]),
                                       delta)))
+        coal = 0
         for i, (t_sub, tk) in enumerate(tickets):
             info = srv.wait(tk)
             k_s.append(info["K"])
+            coal += info["worker"] < 0
             lat_s.append((info["t_end_ms"] - info["t_submit_ms"]) / 1000.0 + t_sub - arrivals[i])
         span_s = time.perf_counter() - t0
-
-    def summ(lat, span):
-        a = np.asarray(lat) * 1000.0
-        return {"p50_ms": float(np.percentile(a, 50)), "p99_ms": float(np.percentile(a, 99)),
-                "qps": Q / span}
-
+        identical = identical and bool(np.array_equal(np.asarray(k_s), np.asarray(k_p)))
+        loads[f"{load:g}x"] = {"offered_qps": rate, "served": summ(lat_s, span_s),
+                               "plain": summ(lat_p, span_p), "coalesced_queries": int(coal)}
+    srv.close()
+    for G in handles:
+        G.close()
+    ns = np.array([g.n for g in gs])
     return {
-        "workload": f"{len(gs)} resident graphs (ER / perturbed grid / Chung-Lu, n log-uniform "
-                    f"on [1e3, {args.serve_nmax:.0e}]), {Q} Kemeny queries, Poisson arrivals at "
-                    f"{args.serve_load}x the plain path's capacity, eps in {{5%, 2%, 1%}}, "
-                    f"delta {delta}",
-        "offered_qps": rate, "workers": args.serve_workers,
-        "served": summ(lat_s, span_s), "plain": summ(lat_p, span_p),
-        "identical_results": bool(np.array_equal(np.asarray(k_s), np.asarray(k_p))),
+        "workload": f"{len(gs)} resident graphs (ER / perturbed grid / Chung-Lu in turn, n "
+                    f"log-uniform on [1e3, {args.serve_nmax:.0e}]: total n {int(ns.sum()):,}, "
+                    f"largest {int(ns.max()):,}), {Q} Kemeny queries per load, Poisson "
+                    f"arrivals, eps in {{5%, 2%, 1%}}, delta {delta}",
+        "graph_gen_s": gen_s, "resident_graph_bytes": resident,
+        "budget_bytes": budget, "request_bytes": per_req, "workers": args.serve_workers,
+        "coalesce_max_n": 1 << 18, "plain_capacity_qps": capacity, "loads": loads,
+        "identical_results": identical,
     }
+
 
 # DRAM bytes per Wilson departure of k_wilson_warp on road-shaped grids, from an
 # ncu capture (dram__bytes) on the 300x300 perturbed grid with 1000 trees in
@@ -708,14 +747,17 @@ def main():
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-other", action="store_true",
                     help="skip the other static workloads (er2000, cl4m)")
-    ap.add_argument("--serve-graphs", type=int, default=48)
-    ap.add_argument("--serve-nmax", type=float, default=3e4)
-    ap.add_argument("--serve-queries", type=int, default=96)
+    ap.add_argument("--serve-graphs", type=int, default=512)
+    ap.add_argument("--serve-nmax", type=float, default=1e6)
+    ap.add_argument("--serve-queries", type=int, default=64)
     ap.add_argument("--serve-workers", type=int, default=8)
+    ap.add_argument("--serve-loads", type=lambda x: [float(v) for v in x.split(",")],
+                    default=[0.8, 1.5],
+                    help="offered loads, as multiples of the plain path's capacity")
     ap.add_argument("--batched-trees", type=int, default=256,
                     help="trees per graph in the batched multi-graph leg")
-    ap.add_argument("--serve-load", type=float, default=1.5,
-                    help="offered query rate as a multiple of the plain path's capacity")
+    ap.add_argument("--batched-graphs", type=int, default=48)
+    ap.add_argument("--batched-nmax", type=float, default=3e4)
     ap.add_argument("--reject-quantile", type=float, default=0.0,
                     help="rejection by walk length with the cap at this quantile of a probe "
                          "batch's step counts (0: off)")

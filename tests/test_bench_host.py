@@ -39,6 +39,10 @@ def test_serving_workload_is_seeded_and_mixed():
     assert all(1 <= g.n <= 5000 for g in a)
     # ER, perturbed grid, Chung-Lu in turn: grids have maximum degree 4
     assert max(a[1].deg) <= 4 and max(a[2].deg) > 4
+    # generation in spawned processes gives the same graphs
+    c = bench.serve_workload(6, 5000, procs=2)
+    assert all(np.array_equal(x.col, y.col) and np.array_equal(x.row_off, y.row_off)
+               for x, y in zip(a, c))
 
 
 def test_reference_arm_prints_one_json_line():
