@@ -334,7 +334,6 @@ def time_to_eps(kc, g, cfg, eps: float, delta: float, batch: int, stream, worklo
     for f, _ in kc.kc_config._fields_:
         setattr(cfg2, f, getattr(cfg, f))
     cfg2.batch_trees = batch
-    cfg2.reject_steps = 0
     H = kc.KemenyGraph.from_graph(g, cfg2, stream=stream.cuda_stream)
     torch.cuda.synchronize()
     t = time.perf_counter()
@@ -758,13 +757,13 @@ def main():
                     help="trees per graph in the batched multi-graph leg")
     ap.add_argument("--batched-graphs", type=int, default=48)
     ap.add_argument("--batched-nmax", type=float, default=3e4)
-    ap.add_argument("--reject-quantile", type=float, default=0.0,
+    ap.add_argument("--reject-quantile", type=float, default=0.8,
                     help="rejection by walk length with the cap at this quantile of a probe "
                          "batch's step counts (0: off)")
     ap.add_argument("--reject-probe", type=int, default=256,
                     help="trees of the probe batch that sets the rejection cap")
-    ap.add_argument("--dynamic", action="store_true",
-                    help="also run the update-stream leg (ISM against BSM)")
+    ap.add_argument("--no-dynamic", action="store_true",
+                    help="skip the dynamic-serving leg (ISM against BSM under an update stream)")
     ap.add_argument("--dyn-n", type=int, default=1000000)
     ap.add_argument("--dyn-updates", type=int, default=32,
                     help="ops of the seeded update stream processed (a prefix)")
@@ -806,11 +805,16 @@ def main():
     if args.reject_quantile > 0:
         # rejection by walk length: the cap is a quantile of the step counts of
         # a probe batch (a rule on step counts only, so the trees stay uniform)
-        P = kc.KemenyGraph.from_graph(g, cfg, stream=stream.cuda_stream)
+        pcfg = kc.kc_config_default()
+        for f, _ in kc.kc_config._fields_:
+            setattr(pcfg, f, getattr(cfg, f))
+        pcfg.walker = kc.KC_WALK_WARP  # a few hundred trees: 32 walkers each finish sooner
+        P = kc.KemenyGraph.from_graph(g, pcfg, stream=stream.cuda_stream)
         P.sample(args.seed, args.reject_probe)
         probe_steps = P.samples()["steps"]
         P.close()
         cfg.reject_steps = max(int(np.quantile(probe_steps, args.reject_quantile)), n - 1)
+        cfg.reject_accept_hint = args.reject_quantile
         reject = {"quantile": args.reject_quantile, "probe_trees": args.reject_probe,
                   "reject_steps": int(cfg.reject_steps)}
     G = kc.KemenyGraph.from_graph(g, cfg, stream=stream.cuda_stream)
@@ -881,8 +885,15 @@ def main():
         # batches of one resident wave where trees are long (deep tau0: a wave
         # lasts about as long as its slowest tree, so a wave of 1024 costs
         # about what a full one does), 1024 trees where waves are throughput-bound
-        deep = st["ttf_variant"] == kc.KC_TTF_BIT and st["walker"] == kc.KC_WALK_WARP
-        batch = max(1024, st["resident_trees"]) if deep else 1024
+        # (with one walker per tree every tree of a wave is in flight at once, so
+        # a pilot large enough for the usual answer costs one wave as well)
+        deep = st["ttf_variant"] == kc.KC_TTF_BIT
+        if deep and st["walker"] == kc.KC_WALK_LANE:
+            batch = 4096
+        elif deep:
+            batch = max(1024, st["resident_trees"])
+        else:
+            batch = 1024
         out["time_to_eps"] = time_to_eps(kc, g, cfg, args.eps, args.delta, batch, stream,
                                          args.workload)
 
@@ -928,7 +939,7 @@ def main():
         out["batched"] = batched_leg(args, kc)
 
     # ---- sample maintenance under an update stream (rank 0, on request)
-    if args.dynamic and rank == 0:
+    if not args.no_dynamic and rank == 0:
         out["dynamic"] = dynamic_leg(args, kc)
 
     # ---- the CPU oracle on the host cores (rank 0, N = 1 only)

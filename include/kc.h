@@ -84,7 +84,8 @@ enum { KC_UPDATE_BSM = 0,      /* Algorithm 2 */
        KC_UPDATE_ISM = 1 };    /* Algorithm 3 */
 
 /* Wilson walkers per tree.  All give identical trees and step counts. */
-enum { KC_WALK_AUTO = 0,       /* WARP                                                    */
+enum { KC_WALK_AUTO = 0,       /* WARP; LANE under rejection by walk length on a graph
+                                  whose TTF variant is BIT (long diameter)                */
        KC_WALK_LANE = 1,       /* one sequential walker per tree (one lane)              */
        KC_WALK_WARP = 2,       /* 32 concurrent walkers per tree popping cycles in any order */
        KC_WALK_HYBRID = 3 };   /* LANE for a prefix of the start order, then WARP for the
@@ -156,6 +157,11 @@ typedef struct {
                                    non-root vertex departs once); needs the LANE or
                                    WARP walker, keep_trees = 0 and no autotune; not
                                    for kc_sample_multi.  0: off (default)           */
+    double reject_accept_hint;  /* expected share of trees within reject_steps (e.g. the
+                                   quantile the cap was taken at), in (0, 1]: sizes a
+                                   handle's first rejection wave so that it usually
+                                   accepts enough trees in one go; later waves use the
+                                   share seen so far.  0: 8/9                       */
 } kc_config;
 
 /* Fill *cfg with the defaults listed above. */

@@ -1217,16 +1217,17 @@ void run_wave_reject(kc_graph *g, Plan &p, int64_t B, int64_t sid0) {
 // evaluated (overlapping the walk, as pipelined waves do, on large graphs) and
 // appended to the pool in sample-id order, until ntrees are accepted.
 // A wave draws about need / rate trees, rate being the acceptance rate seen on
-// this handle so far (1/8 more than needed before any is seen), so that one
+// this handle so far (before any is seen: cfg.reject_accept_hint, else 8/9), so that one
 // wave usually suffices; of its accepted trees only the first `need` in id
 // order are kept, and the ids after the last kept one are left for the next
 // call.  Rejected ids below it are consumed (never reused).
 void do_sample_reject(kc_graph *g, int64_t ntrees) {
+    const double hint = g->cfg.reject_accept_hint > 0 ? g->cfg.reject_accept_hint : 8.0 / 9.0;
     auto wave_size = [&](int64_t need) {
         const double rate = g->rej_drawn > 0
                                 ? std::max(1.0 / 64.0, (double)(g->rej_accepted + 1) /
                                                            (double)(g->rej_drawn + 1))
-                                : 8.0 / 9.0;
+                                : hint;
         // expected draws plus three standard deviations of the accepted count
         const double want = (double)need / rate;
         const double sd = std::sqrt(want * rate * (1.0 - rate)) / rate;
@@ -1676,6 +1677,7 @@ kc_status kc_graph_create(int64_t n, const int64_t *row_off, const int32_t *col,
         return KC_ERR_INVALID_ARG;
     // rejection by walk length: the 32-walker kernel, static pools, and a cap a
     // tree can meet (every non-root vertex departs at least once)
+    if (!(cfg.reject_accept_hint >= 0 && cfg.reject_accept_hint <= 1)) return KC_ERR_INVALID_ARG;
     if (cfg.reject_steps < 0 ||
         (cfg.reject_steps > 0 &&
          (cfg.reject_steps < n - 1 || cfg.keep_trees || cfg.autotune ||
@@ -1811,9 +1813,15 @@ kc_status kc_graph_create(int64_t n, const int64_t *row_off, const int32_t *col,
         // whenever fewer trees fit in memory than it has warp slots, and a wave
         // lasts as long as its slowest tree; 32 walkers per tree finish the
         // long trees of road-shaped graphs about 4 steps per iteration, so they
-        // are the default on every graph.
+        // are the default.  Under rejection by walk length on a long-diameter
+        // graph (BIT variant) no tree walks past the cap, and one walker per
+        // tree keeps every tree of the wave in flight from the start (32-walker
+        // trees wait for one of the SMs' warp slots): the wave then lasts about
+        // cap x one walker's time per departure, which measured shorter.
         int walker = cfg.walker;
-        if (walker == KC_WALK_AUTO || cfg.autotune) walker = KC_WALK_WARP;
+        if (walker == KC_WALK_AUTO || cfg.autotune)
+            walker = (cfg.reject_steps > 0 && !cfg.autotune && variant == KC_TTF_BIT)
+                         ? KC_WALK_LANE : KC_WALK_WARP;
         g->walker = walker;
     } catch (Fail &f) {
         kc_graph_destroy(g);
