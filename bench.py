@@ -708,13 +708,12 @@ def serve_leg(args, kc):
     }
 
 
-# DRAM bytes per Wilson departure of k_wilson_warp on road-shaped grids, from an
-# ncu capture (dram__bytes) on the 300x300 perturbed grid with 1000 trees in
-# flight; the full-size launch is too long to capture, so its traffic is this
-# figure times its departures.  None while no capture of the kernel as built
-# exists (the last one, 10.27 GB for 1.133e9 departures, predates the kernel's
-# multi-graph template).
-WILSON_WARP_GRID_DRAM_BYTES_PER_STEP = None
+# DRAM bytes per Wilson departure of the walkers on road-shaped grids, from ncu
+# captures (dram__bytes_read.sum + dram__bytes_write.sum) on the 300x300
+# perturbed grid with 1000 trees in flight (profiles/); a full-size launch runs
+# for seconds, too long to capture, so its traffic is this figure times its
+# departures.  k_wilson_warp: 10.213 GB for 1,133,364,358 departures.
+WALKER_GRID_DRAM_BYTES_PER_STEP = {"warp": 10.213e9 / 1133364358}
 
 
 def main():
@@ -844,9 +843,8 @@ def main():
     samples = G.samples(pool0, st["pool_trees"] - pool0)
     steps_total = int(samples["steps"].sum())
     trees_timed = T * args.steps
-    traffic_per_step = (WILSON_WARP_GRID_DRAM_BYTES_PER_STEP
-                        if st["walker"] == kc.KC_WALK_WARP and args.workload.startswith("grid")
-                        else None)
+    traffic_per_step = (WALKER_GRID_DRAM_BYTES_PER_STEP.get(WALKER_NAMES[st["walker"]])
+                        if args.workload.startswith("grid") else None)
     dom, roof, phase_ms = phase_roofline(kc, st, n, trees_timed, steps_total, tot_ms,
                                          traffic_per_step)
     roof["traffic_basis"] = (None if roof["traffic"] is None else
