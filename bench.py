@@ -759,6 +759,8 @@ def main():
     ap.add_argument("--reject-quantile", type=float, default=0.8,
                     help="rejection by walk length with the cap at this quantile of a probe "
                          "batch's step counts (0: off)")
+    ap.add_argument("--mem-fraction", type=float, default=0.9,
+                    help="share of free device memory for the sampling workspaces")
     ap.add_argument("--reject-probe", type=int, default=256,
                     help="trees of the probe batch that sets the rejection cap")
     ap.add_argument("--no-dynamic", action="store_true",
@@ -800,6 +802,7 @@ def main():
                   "lane": kc.KC_WALK_LANE, "hybrid": kc.KC_WALK_HYBRID}[args.walker]
     cfg.hybrid_prefix_permille = args.hybrid_prefix
     cfg.hybrid_tail_permille = args.hybrid_tail
+    cfg.mem_fraction = args.mem_fraction
     reject = None
     if args.reject_quantile > 0:
         # rejection by walk length: the cap is a quantile of the step counts of

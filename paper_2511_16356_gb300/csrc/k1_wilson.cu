@@ -42,8 +42,12 @@ __global__ void k_wave_init(int64_t n, int64_t B, int32_t root, uint64_t *word, 
 // abandoned (steps = -1) instead of failing the wave -- rejection by walk
 // length.  With done_flag set, each lane publishes its finished tree to the
 // host (depth + 1, or -1 when rejected) for the pipelined traversal.
+// One-warp blocks: a wave of ten thousand lanes is ~300 warps, fewer than the
+// SMs' schedulers, so each warp runs alone on its scheduler, latency-bound;
+// one-warp blocks spread the warps over every SM (and its L1).
+constexpr int kLaneWalkerBlock = 32;
 template <bool kReject>
-__global__ void __launch_bounds__(128) k_wilson(GraphView g, WaveView w, uint64_t seed,
+__global__ void __launch_bounds__(kLaneWalkerBlock) k_wilson(GraphView g, WaveView w, uint64_t seed,
                                                 const int64_t *__restrict__ sids,
                                                 const int32_t *__restrict__ sorder,
                                                 int64_t step_cap, int32_t *rs_q, int32_t *rs_pos,
@@ -632,16 +636,18 @@ cudaError_t launch_wilson(const GraphView &g, WaveView w, uint64_t seed, const i
                           int64_t step_cap, cudaStream_t s, const int32_t *sorder, int32_t *rs_q,
                           int32_t *rs_pos, unsigned int *done, int64_t q_stop, int64_t stop_at,
                           int32_t *done_flag) {
-    k_wilson<false><<<(unsigned)((w.B + 127) / 128), 128, 0, s>>>(
-        g, w, seed, sids, sorder, step_cap, rs_q, rs_pos, done, q_stop, stop_at, done_flag);
+    k_wilson<false><<<(unsigned)((w.B + kLaneWalkerBlock - 1) / kLaneWalkerBlock),
+                      kLaneWalkerBlock, 0, s>>>(g, w, seed, sids, sorder, step_cap, rs_q, rs_pos,
+                                                done, q_stop, stop_at, done_flag);
     return cudaGetLastError();
 }
 
 cudaError_t launch_wilson_reject(const GraphView &g, WaveView w, uint64_t seed,
                                  const int64_t *sids, const int32_t *sorder, int64_t tree_cap,
                                  cudaStream_t s, int32_t *done_flag) {
-    k_wilson<true><<<(unsigned)((w.B + 127) / 128), 128, 0, s>>>(
-        g, w, seed, sids, sorder, tree_cap, nullptr, nullptr, nullptr, 0, 0, done_flag);
+    k_wilson<true><<<(unsigned)((w.B + kLaneWalkerBlock - 1) / kLaneWalkerBlock),
+                     kLaneWalkerBlock, 0, s>>>(g, w, seed, sids, sorder, tree_cap, nullptr, nullptr,
+                                               nullptr, 0, 0, done_flag);
     return cudaGetLastError();
 }
 

@@ -205,14 +205,14 @@ void ensure_pool(kc_graph *g, int64_t need) {
 
 // Wave sizes within the workspace budget (kc_host_plan.h): the handle's cap,
 // or a share of the device's free memory (counting the workspace it holds).
-Plan plan_for(kc_graph *g, int64_t ntrees, bool canon = true) {
+Plan plan_for(kc_graph *g, int64_t ntrees, bool canon = true, double walker_share = 0.7) {
     size_t free_b = 0, total_b = 0;
     KC_CK(g, cudaMemGetInfo(&free_b, &total_b));
     const double frac = g->cfg.mem_fraction > 0 ? g->cfg.mem_fraction : 0.8;
     const double budget = g->ws_limit > 0 ? (double)g->ws_limit
                                           : (double)(free_b + g->ws_bytes) * frac;
     return kc_host::plan_waves(g->n, ntrees, g->ttf_variant == KC_TTF_BIT, canon, budget,
-                               g->cfg.max_trees_in_flight);
+                               g->cfg.max_trees_in_flight, walker_share);
 }
 
 // DFS stack of the BIT variant: one entry per stacked ancestor, so the
@@ -1234,7 +1234,10 @@ void do_sample_reject(kc_graph *g, int64_t ntrees) {
         return (int64_t)std::ceil(want + 3.0 * sd) + 8;
     };
     ensure_pool(g, g->pool + ntrees);
-    Plan p = plan_for(g, wave_size(ntrees), false);
+    // the wave's accepted trees stream through traversal chunks, so the walk
+    // may take most of the budget: with one walker per tree, every tree of a
+    // wave walks at once and a wave lasts about reject_steps departures
+    Plan p = plan_for(g, wave_size(ntrees), false, 0.9);
     ensure_ws(g, p);
     ensure_pipeline(g, p.BW);  // done flags and tree-map staging
     const int64_t pool0 = g->pool, sid_base = g->next_sid, rej0 = g->trees_rejected;

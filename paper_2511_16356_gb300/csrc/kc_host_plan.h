@@ -9,7 +9,8 @@
 // a separate allocation sized after the walk.  Low-eccentricity graphs (tau0
 // scan) spend more time in the traversal than in the walk, so both get the same
 // count; long-diameter graphs (BIT) spend most of it walking, which gets 70% of
-// the budget (less when that would leave no room for one sub-wave tree).
+// the budget by default (less when that would leave no room for one sub-wave
+// tree).
 //
 // Plain C++ (no CUDA): the same header is compiled by the host tests.
 #pragma once
@@ -48,9 +49,11 @@ inline size_t ws_bytes(int64_t n_vertices, const Plan &p) {
 }
 
 // Wave sizes for ntrees trees within `budget` bytes (at least one tree each;
-// max_in_flight > 0 caps the wave).
+// max_in_flight > 0 caps the wave).  walker_share: the part of the budget the
+// BIT variant gives to the Wilson wave (0.7; waves whose traversal streams
+// through chunks of finished trees can give it more).
 inline Plan plan_waves(int64_t n_vertices, int64_t ntrees, bool bit, bool canon, double budget,
-                       int64_t max_in_flight) {
+                       int64_t max_in_flight, double walker_share = 0.7) {
     Plan p;
     p.bit = bit;
     p.canon = canon;
@@ -60,7 +63,7 @@ inline Plan plan_waves(int64_t n_vertices, int64_t ntrees, bool bit, bool canon,
                          (p.bit ? 16.0 * 4096.0 : 0.0);
     int64_t bw, bt;
     if (p.bit) {
-        bw = (int64_t)std::floor(0.7 * budget / per_w);
+        bw = (int64_t)std::floor(walker_share * budget / per_w);
         // leave room for at least one sub-wave tree
         bw = std::min<int64_t>(bw, (int64_t)std::floor((budget - per_t) / per_w));
         bw = std::max<int64_t>(1, std::min<int64_t>(bw, ntrees));

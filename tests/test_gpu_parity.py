@@ -453,3 +453,22 @@ def test_autotuner_pilots_keep_trees_bit_exact(name):
         f_ref, st_ref = O.sample_batch(g, t0, 13, 0, 250)
         assert np.array_equal(got["steps"], st_ref)
         assert np.array_equal(got["f"], f_ref)
+
+
+@pytest.mark.parametrize("name,trees", [("cl80000", 96), ("grid300x300", 16)])
+def test_lane_walker_pipelined_waves_bit_exact(name, trees):
+    """One walker per tree on graphs large enough for pipelined waves: every
+    lane flags its finished tree (depth + 1) for the traversal and TTF chunks
+    on the second stream; f and step counts equal the oracle's, sample ids in
+    order, and a retained tree's arrays equal the oracle's."""
+    g = S.chung_lu(80000, 2.1, 10.0, 6) if name == "cl80000" else S.workload("grid300x300")
+    t0 = O.tau0(g)
+    seed = 31
+    with kc.KemenyGraph.from_graph(g, _cfg(keep_trees=0, walker=kc.KC_WALK_LANE)) as G:
+        G.sample(seed, trees)
+        got = G.samples()
+        assert G.stats()["walker"] == kc.KC_WALK_LANE
+    f_ref, st_ref = O.sample_batch(g, t0, seed, 0, trees)
+    assert np.array_equal(got["sid"], np.arange(trees))
+    assert np.array_equal(got["steps"], st_ref)
+    assert np.array_equal(got["f"], f_ref)
