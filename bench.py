@@ -581,7 +581,10 @@ def dynamic_leg(args, kc):
                      "query_p99_ms": float(np.percentile(q_ms, 99)),
                      "trees_resampled": int(st["trees_resampled"]),
                      "pool_trees": int(st["pool_trees"]), "pool_build_s": pool_s,
-                     "K_before": k0, "K_after": k_hat, "last_cg_iters": int(st["last_cg_iters"])}
+                     "K_before": k0, "K_after": k_hat, "last_cg_iters": int(st["last_cg_iters"]),
+                     "ms_per_op_by_part": {
+                         k: st[f"ms_update_{k}"] / max(1, ops_n)
+                         for k in ("graph", "resistance", "trees", "refresh")}}
     # reference: a fresh pool of the same size on the final graph
     ins = {(min(u, v), max(u, v)) for b in batches for u, v, op in b if op == 0}
     dele = {(min(u, v), max(u, v)) for b in batches for u, v, op in b if op == 1}

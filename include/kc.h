@@ -335,6 +335,10 @@ typedef struct {
                                    up to this many trees lasts about as long as its
                                    slowest tree, so it is the natural kc_estimate
                                    batch where single trees are slow            */
+    /* kc_update wall time by part (ms; each part ends in a stream synchronisation):
+       the device graph edit, R(u,v), the tree selection and transformation
+       (link-cut / cut-link) or resampling, and the recomputation of f           */
+    double ms_update_graph, ms_update_resistance, ms_update_trees, ms_update_refresh;
 } kc_stats_t;
 
 kc_status kc_stats(kc_graph *g, kc_stats_t *out);

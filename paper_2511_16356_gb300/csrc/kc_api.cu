@@ -750,6 +750,17 @@ kc_status validate_batch(kc_graph *g, const kc_edge_op *ops, int64_t n_ops) {
     return KC_OK;
 }
 
+// Host wall time of one part of an update (every part ends synchronised).
+struct UpdPart {
+    double &acc;
+    std::chrono::steady_clock::time_point t0 = std::chrono::steady_clock::now();
+    explicit UpdPart(double &a) : acc(a) {}
+    ~UpdPart() {
+        acc += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0)
+                   .count();
+    }
+};
+
 // One op on the device CSR (rows kept sorted), then the walk records and
 // degrees of the changed graph; the host copy of the CSR is refreshed once per
 // batch (sync_host_csr).  Nothing goes through the host per op but the check
@@ -854,6 +865,7 @@ void check_err(kc_graph *g, const char *what) {
 // traversal and f(tau) of the retained trees at `slots`, on the current graph
 void refresh_slots(kc_graph *g, const std::vector<int64_t> &slots) {
     if (slots.empty()) return;
+    UpdPart tp(g->ms_upd_part[3]);
     GraphView gv = view_of(g);
     Plan p = plan_for(g, (int64_t)slots.size());
     ensure_ws(g, p);
@@ -983,11 +995,15 @@ double weight_sum(kc_graph *g, const std::vector<uint8_t> &flags, int which) {
 }
 
 void apply_insert(kc_graph *g, int32_t u, int32_t v, int32_t mode, double r_given) {
-    edit_graph(g, u, v, true);
+    {
+        UpdPart tp(g->ms_upd_part[0]);
+        edit_graph(g, u, v, true);
+    }
     // the BIT kernel holds 2m in 32 bits; the scan gives the same f on any graph
     if (g->ttf_variant == KC_TTF_BIT && 2 * g->m >= ((int64_t)1 << 31)) g->ttf_variant = KC_TTF_SCAN;
     double R = r_given;
     if (g->cfg.r_source != KC_R_GIVEN) {
+        UpdPart tp(g->ms_upd_part[1]);
         int nl = 0;
         int64_t iters = 0;
         if (!g->d_cg) dalloc(g, &g->d_cg, cg_scratch_doubles(g->n));
@@ -997,6 +1013,7 @@ void apply_insert(kc_graph *g, int32_t u, int32_t v, int32_t mode, double r_give
         g->last_cg_iters = iters;
     }
     g->last_r = R;
+    UpdPart tp(g->ms_upd_part[2]);
     const int64_t N = g->pool;
     const int64_t k = std::min<int64_t>(N, (int64_t)std::ceil(R * (double)N));
     UpdBuf ub = upd_buf(g);
@@ -1029,6 +1046,7 @@ void apply_insert(kc_graph *g, int32_t u, int32_t v, int32_t mode, double r_give
 }
 
 void apply_delete(kc_graph *g, int32_t u, int32_t v, int32_t mode) {
+    UpdPart tp(g->ms_upd_part[2]);  // the graph edit and tau0 rebuild are moved out below
     const int64_t N = g->pool;
     UpdBuf ub = upd_buf(g);
     KC_CK(g, launch_contains_edge(g->n, N, g->d_parents, u, v, ub.flags, g->stream));
@@ -1045,6 +1063,7 @@ void apply_delete(kc_graph *g, int32_t u, int32_t v, int32_t mode) {
     const bool tau0_hit = (pu == v) || (pv == u);
     double w_org = 0.0;
     if (mode == KC_UPDATE_ISM) w_org = weight_sum(g, flags, 0);
+    const auto tg0 = std::chrono::steady_clock::now();
     edit_graph(g, u, v, false);
     if (tau0_hit) {
         int nl = 0;
@@ -1057,6 +1076,12 @@ void apply_delete(kc_graph *g, int32_t u, int32_t v, int32_t mode) {
         nl = 0;
         traverse_tau0(g, nl);
         g->t_update.launches += nl;
+    }
+    {
+        const double ms = std::chrono::duration<double, std::milli>(
+                              std::chrono::steady_clock::now() - tg0).count();
+        g->ms_upd_part[0] += ms;
+        g->ms_upd_part[2] -= ms;  // tp adds the whole function at its end
     }
     if (mode == KC_UPDATE_BSM) {
         resample_slots(g, hit, false, u, v);
@@ -2147,6 +2172,10 @@ kc_status kc_stats(kc_graph *g, kc_stats_t *out) {
     out->launches_reduce = g->t_reduce.launches;
     out->launches_update = g->t_update.launches;
     out->launches_setup = g->t_setup.launches;
+    out->ms_update_graph = g->ms_upd_part[0];
+    out->ms_update_resistance = g->ms_upd_part[1];
+    out->ms_update_trees = g->ms_upd_part[2] - g->ms_upd_part[3];  // refreshes timed apart
+    out->ms_update_refresh = g->ms_upd_part[3];
     if (g->pool > 0) {
         try {
             std::vector<int64_t> st((size_t)g->pool);
@@ -2224,6 +2253,7 @@ kc_status kc_reset_timers(kc_graph *g) {
     if (!g) return KC_ERR_INVALID_ARG;
     g->t_wilson = g->t_traverse = g->t_ttf = g->t_reduce = g->t_update = g->t_setup =
         g->t_init = PhaseTimer();
+    for (double &x : g->ms_upd_part) x = 0.0;
     return KC_OK;
 }
 

@@ -257,6 +257,7 @@ struct kc_graph {
     double last_r = 0.0;
     int64_t last_cg_iters = 0;
     kc::PhaseTimer t_wilson, t_traverse, t_ttf, t_reduce, t_update, t_setup, t_init;
+    double ms_upd_part[4] = {0, 0, 0, 0};  // kc_update: graph edit, R, trees, refresh
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     // pipelined waves: a second stream for traversal/TTF chunks, host-mapped
     // per-tree completion flags written by the walker, the chunks' tree maps

@@ -75,6 +75,8 @@ _STATS_FIELDS = [
     ("traversal", ctypes.c_int32), ("tuned", ctypes.c_int32),
     ("tune_ms", ctypes.c_double * 4), ("trees_rejected", ctypes.c_int64),
     ("resident_trees", ctypes.c_int64),
+    ("ms_update_graph", ctypes.c_double), ("ms_update_resistance", ctypes.c_double),
+    ("ms_update_trees", ctypes.c_double), ("ms_update_refresh", ctypes.c_double),
 ]
 
 
