@@ -759,7 +759,7 @@ def main():
                     help="trees per graph in the batched multi-graph leg")
     ap.add_argument("--batched-graphs", type=int, default=48)
     ap.add_argument("--batched-nmax", type=float, default=3e4)
-    ap.add_argument("--reject-quantile", type=float, default=0.8,
+    ap.add_argument("--reject-quantile", type=float, default=0.65,
                     help="rejection by walk length with the cap at this quantile of a probe "
                          "batch's step counts (0: off)")
     ap.add_argument("--mem-fraction", type=float, default=0.9,
