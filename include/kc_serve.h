@@ -46,8 +46,10 @@ typedef struct {
                                (kc_sample_multi); queries join and leave between rounds.
                                Each query draws the same trees and takes the same
                                stopping decisions as kc_estimate, so its K is the one
-                               it gets alone.  Larger graphs, and graphs with the
-                               Hoeffding rule, rejection or the autotuner, stay with
+                               it gets alone.  Larger graphs, graphs whose path tree
+                               is deep (the BIT variant: long walks, which would hold
+                               up every query of a round), and graphs with the
+                               Hoeffding rule, rejection or the autotuner stay with
                                the workers.  0: off                                 */
     int32_t reserved;
     int64_t coalesce_max_n; /* 0: 2^18                                                */

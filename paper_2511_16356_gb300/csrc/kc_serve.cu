@@ -395,7 +395,12 @@ kc_status kc_server_add_graph(kc_server *s, int64_t n, const int64_t *row_off, c
     g.n = n;
     g.dynamic = pool_trees > 0;
     g.cfg = cfg;
-    g.coalesced = s->cfg.coalesce && !g.dynamic && n <= s->cfg.coalesce_max_n &&
+    // a round lasts as long as its slowest walk: graphs with a deep tau0 (the
+    // BIT variant: long walks, e.g. road-shaped ones) stay with the workers
+    kc_stats_t stt;
+    std::memset(&stt, 0, sizeof(stt));
+    const bool shallow = kc_stats(h, &stt) == KC_OK && stt.ttf_variant == KC_TTF_SCAN;
+    g.coalesced = s->cfg.coalesce && !g.dynamic && n <= s->cfg.coalesce_max_n && shallow &&
                   cfg.stop_rule == KC_STOP_CLT && cfg.reject_steps == 0 && !cfg.autotune;
     s->graphs.push_back(g);
     *graph_id = (int32_t)(s->graphs.size() - 1);
