@@ -62,6 +62,7 @@ __global__ void __launch_bounds__(kLaneWalkerBlock) k_wilson(GraphView g, WaveVi
     int32_t *__restrict__ ord = w.ord + t * n;
     const VRec *__restrict__ rec = g.rec;
     const uint32_t sample = (uint32_t)sids[t];
+    const PhiloxKeys keys = philox_keys(seed);
 
     int64_t steps = 0;
     int32_t pos = w.pos0;  // ord[0 .. pos0) already placed (the root, or an edge)
@@ -84,8 +85,8 @@ __global__ void __launch_bounds__(kLaneWalkerBlock) k_wilson(GraphView g, WaveVi
         int32_t a;
         bool want_rec = true;
         if (phase == kWalk) {
-            const uint32_t k = bounded_draw(seed, (uint32_t)u, w_count(wu), sample, kTagWalk,
-                                            (uint32_t)ru.deg);
+            const uint32_t k = bounded_draw_k(keys, seed, (uint32_t)u, w_count(wu), sample,
+                                              kTagWalk, (uint32_t)ru.deg);
             int32_t v;
             if (k < (uint32_t)kInline) {
                 // register select instead of a dynamic index into the record
@@ -318,6 +319,7 @@ __global__ void __launch_bounds__(kWarpWalkerBlock, 24)
     int32_t *ord = w.ord + t * n;
     const VRec *__restrict__ rec = g.rec;
     const uint32_t sample = (uint32_t)sids[t];
+    const PhiloxKeys keys = philox_keys(seed);
 
     int ph = pIdle;
     bool has_path = false;
@@ -366,8 +368,8 @@ __global__ void __launch_bounds__(kWarpWalkerBlock, 24)
         // ---- act: departures and the address each lane reads this iteration
         int32_t ld = -1;
         if (ph == pWalk) {
-            const uint32_t k = bounded_draw(seed, (uint32_t)c, cc, sample, kTagWalk,
-                                            (uint32_t)rc.deg);
+            const uint32_t k = bounded_draw_k(keys, seed, (uint32_t)c, cc, sample, kTagWalk,
+                                              (uint32_t)rc.deg);
             const int32_t v = rec_neighbor(rc, g.col, k);
             st_word(word + c, o_own(v, cc + 1, lane));
             cc += 1;

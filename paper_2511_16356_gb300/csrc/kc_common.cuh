@@ -45,6 +45,41 @@ __device__ __forceinline__ void philox4x32_10(uint32_t c0, uint32_t c1, uint32_t
     out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
 }
 
+// The ten round keys of a Philox4x32-10 key: the key schedule adds the Weyl
+// constants once per round and depends on the seed only, so a walker computes
+// it once and its draws skip the twenty additions.
+struct PhiloxKeys {
+    uint32_t k0[10], k1[10];
+};
+__device__ __forceinline__ PhiloxKeys philox_keys(uint64_t seed) {
+    PhiloxKeys K;
+    uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+#pragma unroll
+    for (int i = 0; i < 10; ++i) {
+        K.k0[i] = k0;
+        K.k1[i] = k1;
+        k0 += kPhiloxW0;
+        k1 += kPhiloxW1;
+    }
+    return K;
+}
+// philox4x32_10 with the round keys precomputed
+__device__ __forceinline__ void philox4x32_10_k(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                                const PhiloxKeys &K, uint32_t out[4]) {
+#pragma unroll
+    for (int i = 0; i < 10; ++i) {
+        const uint32_t lo0 = kPhiloxM0 * c0;
+        const uint32_t hi0 = __umulhi(kPhiloxM0, c0);
+        const uint32_t lo1 = kPhiloxM1 * c2;
+        const uint32_t hi1 = __umulhi(kPhiloxM1, c2);
+        c0 = hi1 ^ c1 ^ K.k0[i];
+        c1 = lo1;
+        c2 = hi0 ^ c3 ^ K.k1[i];
+        c3 = lo0;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
 // Uniform integer in [0, s), s >= 1: all four words and the retry counter.
 static __device__ __noinline__ uint32_t bounded_draw_full(uint64_t seed, uint32_t c0, uint32_t c1,
                                                    uint32_t c2, uint32_t tag, uint32_t s) {
@@ -73,6 +108,17 @@ __device__ __forceinline__ uint32_t bounded_draw(uint64_t seed, uint32_t c0, uin
                                                  uint32_t c2, uint32_t tag, uint32_t s) {
     uint32_t w[4];
     philox4x32_10(c0, c1, c2, tag << 24, (uint32_t)seed, (uint32_t)(seed >> 32), w);
+    const uint64_t m = (uint64_t)w[0] * (uint64_t)s;
+    if (__builtin_expect((uint32_t)m >= s, 1)) return (uint32_t)(m >> 32);
+    return bounded_draw_full(seed, c0, c1, c2, tag, s);
+}
+
+// bounded_draw with precomputed round keys (same result)
+__device__ __forceinline__ uint32_t bounded_draw_k(const PhiloxKeys &K, uint64_t seed, uint32_t c0,
+                                                   uint32_t c1, uint32_t c2, uint32_t tag,
+                                                   uint32_t s) {
+    uint32_t w[4];
+    philox4x32_10_k(c0, c1, c2, tag << 24, K, w);
     const uint64_t m = (uint64_t)w[0] * (uint64_t)s;
     if (__builtin_expect((uint32_t)m >= s, 1)) return (uint32_t)(m >> 32);
     return bounded_draw_full(seed, c0, c1, c2, tag, s);
