@@ -588,63 +588,6 @@ __global__ void __launch_bounds__(kWarpWalkerBlock, 24)
     }
 }
 
-// The walk records of a graph (one 32-byte sector per vertex, read by every
-// tree's walkers) are kept in L2 with a persisting access-policy window on the
-// walker launches, so the per-tree walker words streaming through L2 do not
-// evict them.  The set-aside size is a limit of this process's context (it
-// ends with the process); it is raised once per device to the device's maximum,
-// which other accesses may use while no persisting lines claim it.
-bool records_window(const GraphView &g, cudaAccessPolicyWindow *w) {
-    static int set_for[64] = {0};  // per device: 0 unknown, 1 usable, -1 not
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
-        (void)cudaGetLastError();
-        return false;
-    }
-    static int max_window[64] = {0};
-    static size_t persist[64] = {0};
-    if (set_for[dev] == 0) {
-        int mp = 0, mw = 0;
-        if (cudaDeviceGetAttribute(&mp, cudaDevAttrMaxPersistingL2CacheSize, dev) != cudaSuccess ||
-            cudaDeviceGetAttribute(&mw, cudaDevAttrMaxAccessPolicyWindowSize, dev) != cudaSuccess ||
-            mp <= 0 || mw <= 0 ||
-            cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, (size_t)mp) != cudaSuccess) {
-            (void)cudaGetLastError();
-            set_for[dev] = -1;
-            return false;
-        }
-        max_window[dev] = mw;
-        persist[dev] = (size_t)mp;
-        set_for[dev] = 1;
-    }
-    if (set_for[dev] < 0) return false;
-    const size_t bytes = std::min(sizeof(VRec) * (size_t)g.n, (size_t)max_window[dev]);
-    w->base_ptr = (void *)g.rec;
-    w->num_bytes = bytes;
-    w->hitRatio = bytes <= persist[dev] ? 1.0f : (float)((double)persist[dev] / (double)bytes);
-    w->hitProp = cudaAccessPropertyPersisting;
-    w->missProp = cudaAccessPropertyStreaming;
-    return true;
-}
-
-// <<<grid, block, 0, s>>> with the records window when the device has one
-template <class... KArgs, class... Args>
-cudaError_t launch_walker(const GraphView &g, unsigned grid, unsigned block, cudaStream_t s,
-                          void (*kernel)(KArgs...), Args... args) {
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(grid);
-    cfg.blockDim = dim3(block);
-    cfg.dynamicSmemBytes = 0;
-    cfg.stream = s;
-    cudaLaunchAttribute attr[1];
-    if (records_window(g, &attr[0].val.accessPolicyWindow)) {
-        attr[0].id = cudaLaunchAttributeAccessPolicyWindow;
-        cfg.attrs = attr;
-        cfg.numAttrs = 1;
-    }
-    return cudaLaunchKernelEx(&cfg, kernel, args...);
-}
-
 }  // namespace
 
 cudaError_t launch_wilson_warp(const GraphView &g, WaveView w, uint64_t seed, const int64_t *sids,
@@ -653,9 +596,9 @@ cudaError_t launch_wilson_warp(const GraphView &g, WaveView w, uint64_t seed, co
     // a correct run needs at most about 3 iterations per departure (walk,
     // count, commit / pop), however the walkers serialise
     const int64_t iter_cap = 4 * step_cap + 64 * g.n + 4096;
-    return launch_walker(g, (unsigned)w.B, kWarpWalkerBlock, s, k_wilson_warp<false, false>, g, w,
-                         seed, sids, sorder, step_cap, iter_cap, rs_q, rs_pos,
-                         (volatile int32_t *)done_flag, MultiWalk{});
+    k_wilson_warp<false, false><<<(unsigned)w.B, kWarpWalkerBlock, 0, s>>>(
+        g, w, seed, sids, sorder, step_cap, iter_cap, rs_q, rs_pos, done_flag, MultiWalk{});
+    return cudaGetLastError();
 }
 
 cudaError_t launch_wilson_warp_reject(const GraphView &g, WaveView w, uint64_t seed,
@@ -664,9 +607,9 @@ cudaError_t launch_wilson_warp_reject(const GraphView &g, WaveView w, uint64_t s
     // tree_cap bounds the whole tree's departures, and an iteration may move
     // as little as one lane: a generous bound that no accepted tree reaches
     const int64_t iter_cap = 16 * std::min<int64_t>(tree_cap, (int64_t)1 << 40) + 64 * g.n + 4096;
-    return launch_walker(g, (unsigned)w.B, kWarpWalkerBlock, s, k_wilson_warp<false, true>, g, w,
-                         seed, sids, sorder, tree_cap, iter_cap, (const int32_t *)nullptr,
-                         (const int32_t *)nullptr, (volatile int32_t *)done_flag, MultiWalk{});
+    k_wilson_warp<false, true><<<(unsigned)w.B, kWarpWalkerBlock, 0, s>>>(
+        g, w, seed, sids, sorder, tree_cap, iter_cap, nullptr, nullptr, done_flag, MultiWalk{});
+    return cudaGetLastError();
 }
 
 int wilson_warp_blocks_per_sm() {
@@ -697,18 +640,19 @@ cudaError_t launch_wilson(const GraphView &g, WaveView w, uint64_t seed, const i
                           int64_t step_cap, cudaStream_t s, const int32_t *sorder, int32_t *rs_q,
                           int32_t *rs_pos, unsigned int *done, int64_t q_stop, int64_t stop_at,
                           int32_t *done_flag) {
-    return launch_walker(g, (unsigned)((w.B + kLaneWalkerBlock - 1) / kLaneWalkerBlock),
-                         kLaneWalkerBlock, s, k_wilson<false>, g, w, seed, sids, sorder, step_cap,
-                         rs_q, rs_pos, done, q_stop, stop_at, (volatile int32_t *)done_flag);
+    k_wilson<false><<<(unsigned)((w.B + kLaneWalkerBlock - 1) / kLaneWalkerBlock),
+                      kLaneWalkerBlock, 0, s>>>(g, w, seed, sids, sorder, step_cap, rs_q, rs_pos,
+                                                done, q_stop, stop_at, done_flag);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_wilson_reject(const GraphView &g, WaveView w, uint64_t seed,
                                  const int64_t *sids, const int32_t *sorder, int64_t tree_cap,
                                  cudaStream_t s, int32_t *done_flag) {
-    return launch_walker(g, (unsigned)((w.B + kLaneWalkerBlock - 1) / kLaneWalkerBlock),
-                         kLaneWalkerBlock, s, k_wilson<true>, g, w, seed, sids, sorder, tree_cap,
-                         (int32_t *)nullptr, (int32_t *)nullptr, (unsigned int *)nullptr,
-                         (int64_t)0, (int64_t)0, (volatile int32_t *)done_flag);
+    k_wilson<true><<<(unsigned)((w.B + kLaneWalkerBlock - 1) / kLaneWalkerBlock),
+                     kLaneWalkerBlock, 0, s>>>(g, w, seed, sids, sorder, tree_cap, nullptr, nullptr,
+                                               nullptr, 0, 0, done_flag);
+    return cudaGetLastError();
 }
 
 }  // namespace kc
