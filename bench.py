@@ -369,6 +369,7 @@ def other_workload_leg(args, kc, stream, flush, name: str, T: int, steps: int, w
     g = S.workload(name)
     cfg = kc.kc_config_default()
     cfg.keep_trees = 0
+    cfg.autotune = 1  # the first warm-up call times both walkers and keeps the faster
     G = kc.KemenyGraph.from_graph(g, cfg, stream=stream.cuda_stream)
     G.reserve(T * (warmup + steps))
     for _ in range(warmup):
@@ -388,7 +389,11 @@ def other_workload_leg(args, kc, stream, flush, name: str, T: int, steps: int, w
            "value": T * steps / (tot_ms / 1000.0), "unit": "trees/s",
            "ms_per_step": tot_ms / steps, "roofline": roof, "phase_ms": phase_ms,
            "steps_per_tree": steps_total / (T * steps),
-           "ttf": "BIT" if st["ttf_variant"] == kc.KC_TTF_BIT else "SCAN"}
+           "ttf": "BIT" if st["ttf_variant"] == kc.KC_TTF_BIT else "SCAN",
+           "walker": WALKER_NAMES[st["walker"]], "autotune_ms": st["tune_ms"]}
+    # time to eps with the walker the autotuner chose (no tuning inside the timing)
+    cfg.autotune = 0
+    cfg.walker = st["walker"]
     out["time_to_eps"] = time_to_eps(kc, g, cfg, args.eps, delta, 1024, stream, name)
     return out
 
