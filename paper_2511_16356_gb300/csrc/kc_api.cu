@@ -972,8 +972,12 @@ void transform_slots(kc_graph *g, const std::vector<int64_t> &slots, bool insert
         w.B = b;
         KC_CK(g, launch_prepare_from_parents(g->n, b, g->root, g->d_parents, ub.slots, w,
                                              g->stream));
+        // link-cut reads the DFN only to test subtree membership, so any valid
+        // DFN serves (the warp-per-tree pass); cut-link picks the k-th crossing
+        // edge in the id-ordered preorder, which the canonical pass gives
         int nl = 0;
-        KC_CK(g, launch_traverse(gv, w, true, g->stream, &nl));
+        KC_CK(g, launch_traverse(gv, w, true, g->stream, &nl,
+                                 insert ? kTravChunked : kTravCanonical));
         KC_CK(g, launch_link_cut(g->d_row_off, g->d_col, w, ub.slots, g->d_parents, ub.factor,
                                  g->root, u, v, g->seed, (uint32_t)g->update_seq, insert,
                                  g->stream));
