@@ -824,9 +824,14 @@ def main():
         probe_steps = P.samples()["steps"]
         P.close()
         cfg.reject_steps = max(int(np.quantile(probe_steps, args.reject_quantile)), n - 1)
-        cfg.reject_accept_hint = args.reject_quantile
+        # the probe's quantile estimates the acceptance rate with a standard
+        # error of sqrt(q (1 - q) / probe); a hint three errors lower makes a
+        # fresh handle's first wave (time to eps, end to end) rarely fall short
+        se = math.sqrt(args.reject_quantile * (1 - args.reject_quantile) / args.reject_probe)
+        cfg.reject_accept_hint = max(0.05, args.reject_quantile - 3 * se)
         reject = {"quantile": args.reject_quantile, "probe_trees": args.reject_probe,
-                  "reject_steps": int(cfg.reject_steps)}
+                  "reject_steps": int(cfg.reject_steps),
+                  "accept_hint": float(cfg.reject_accept_hint)}
     G = kc.KemenyGraph.from_graph(g, cfg, stream=stream.cuda_stream)
     st0 = G.stats()
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.int32, device="cuda")

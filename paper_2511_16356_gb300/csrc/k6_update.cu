@@ -255,15 +255,20 @@ __global__ void __launch_bounds__(128) k_link_cut(TransformIn a, int64_t B) {
         reroot_chain(a.pool_parents + a.slot[t] * n, side, x, side == a.u ? a.v : a.u, n, a.err);
     }
     x = __shfl_sync(kFull, x, 0);
-    // edges of G' other than e that cross Sub(tau, x)
+    // edges of G' other than e that cross Sub(tau, x): an edge crosses the cut
+    // from either side, so the scan runs over the smaller side (the preorder
+    // positions of Sub(tau, x), or all the others)
     const int32_t lo = din[x], hi = din[x] + sz[x] - 1;
+    const bool inside = 2 * (int64_t)sz[x] <= n;
+    const int64_t span = inside ? (int64_t)sz[x] : n - sz[x];
     long long cross = 0;
-    for (int64_t q = lo + lane; q <= hi; q += 32) {
+    for (int64_t k = lane; k < span; k += 32) {
+        const int64_t q = inside ? lo + k : (k < lo ? k : k + sz[x]);
         const int32_t y = pre[q];
         for (int64_t e = a.row_off[y]; e < a.row_off[y + 1]; ++e) {
             const int32_t z = a.col[e];
             const int32_t dz = din[z];
-            if (dz >= lo && dz <= hi) continue;
+            if ((dz >= lo && dz <= hi) == inside) continue;  // both ends on the scanned side
             if ((y == a.u && z == a.v) || (y == a.v && z == a.u)) continue;
             ++cross;
         }

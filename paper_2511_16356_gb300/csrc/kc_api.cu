@@ -205,24 +205,14 @@ void ensure_pool(kc_graph *g, int64_t need) {
 
 // Wave sizes within the workspace budget (kc_host_plan.h): the handle's cap,
 // or a share of the device's free memory (counting the workspace it holds).
-Plan plan_for(kc_graph *g, int64_t ntrees, bool canon = true, double walker_share = 0.7,
-              bool split = false) {
+Plan plan_for(kc_graph *g, int64_t ntrees, bool canon = true, double walker_share = 0.7) {
     size_t free_b = 0, total_b = 0;
     KC_CK(g, cudaMemGetInfo(&free_b, &total_b));
     const double frac = g->cfg.mem_fraction > 0 ? g->cfg.mem_fraction : 0.8;
     const double budget = g->ws_limit > 0 ? (double)g->ws_limit
                                           : (double)(free_b + g->ws_bytes) * frac;
     return kc_host::plan_waves(g->n, ntrees, g->ttf_variant == KC_TTF_BIT, canon, budget,
-                               g->cfg.max_trees_in_flight, walker_share, split);
-}
-
-// Waves of kc_sample.  Large graphs run pipelined waves (traversal chunks of
-// finished trees on a second stream), so the walk may take most of the budget
-// on shallow graphs too, filling the walker's slots with more trees per wave.
-Plan sample_plan(kc_graph *g, int64_t ntrees) {
-    const bool piped = g->n >= (1 << 16) && !g->cfg.autotune &&
-                       (g->walker == KC_WALK_WARP || g->walker == KC_WALK_LANE);
-    return plan_for(g, ntrees, false, 0.7, piped);
+                               g->cfg.max_trees_in_flight, walker_share);
 }
 
 // DFS stack of the BIT variant: one entry per stacked ancestor, so the
@@ -1364,7 +1354,7 @@ void do_sample(kc_graph *g, int64_t ntrees) {
         return;
     }
     ensure_pool(g, g->pool + ntrees);
-    Plan p = sample_plan(g, ntrees);
+    Plan p = plan_for(g, ntrees, false);
     ensure_ws(g, p);
     const int64_t pool0 = g->pool, sid_base = g->next_sid;
     int64_t done = 0;
@@ -1934,7 +1924,7 @@ kc_status kc_reserve(kc_graph *g, int64_t n_trees) {
     if (n_trees == 0) return KC_OK;
     try {
         ensure_pool(g, g->pool + n_trees);
-        Plan p = sample_plan(g, n_trees);
+        Plan p = plan_for(g, n_trees, false);
         ensure_ws(g, p);
         if (g->walker == KC_WALK_WARP) ensure_pipeline(g, p.BW);
         KC_CK(g, cudaStreamSynchronize(g->stream));

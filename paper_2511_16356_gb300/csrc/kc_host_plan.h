@@ -52,11 +52,8 @@ inline size_t ws_bytes(int64_t n_vertices, const Plan &p) {
 // max_in_flight > 0 caps the wave).  walker_share: the part of the budget the
 // BIT variant gives to the Wilson wave (0.7; waves whose traversal streams
 // through chunks of finished trees can give it more).
-// split: the SCAN variant splits the budget too (walk waves whose traversal
-// streams through chunks of finished trees) instead of giving the walk and
-// the traversal the same count.
 inline Plan plan_waves(int64_t n_vertices, int64_t ntrees, bool bit, bool canon, double budget,
-                       int64_t max_in_flight, double walker_share = 0.7, bool split = false) {
+                       int64_t max_in_flight, double walker_share = 0.7) {
     Plan p;
     p.bit = bit;
     p.canon = canon;
@@ -65,7 +62,7 @@ inline Plan plan_waves(int64_t n_vertices, int64_t ntrees, bool bit, bool canon,
     const double per_t = (p.bit ? 28.0 : (canon ? 20.0 : 16.0)) * n + 64.0 +
                          (p.bit ? 16.0 * 4096.0 : 0.0);
     int64_t bw, bt;
-    if (p.bit || split) {
+    if (p.bit) {
         bw = (int64_t)std::floor(walker_share * budget / per_w);
         // leave room for at least one sub-wave tree
         bw = std::min<int64_t>(bw, (int64_t)std::floor((budget - per_t) / per_w));

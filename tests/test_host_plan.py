@@ -16,10 +16,10 @@ CSRC = os.path.join(ROOT, "paper_2511_16356_gb300", "csrc")
 SHIM = r"""
 #include "kc_host_plan.h"
 extern "C" void hp_plan(int64_t n, int64_t ntrees, int bit, int canon, double budget,
-                        int64_t max_in_flight, double share, int split, int64_t *bw,
-                        int64_t *bt, uint64_t *bytes) {
+                        int64_t max_in_flight, double share, int64_t *bw, int64_t *bt,
+                        uint64_t *bytes) {
     const kc_host::Plan p = kc_host::plan_waves(n, ntrees, bit != 0, canon != 0, budget,
-                                                max_in_flight, share, split != 0);
+                                                max_in_flight, share);
     *bw = p.BW;
     *bt = p.BT;
     *bytes = kc_host::ws_bytes(n, p);
@@ -39,13 +39,13 @@ def plan(tmp_path_factory):
     lib = ctypes.CDLL(str(d / "shim.so"))
     lib.hp_plan.restype = None
     lib.hp_plan.argtypes = [ctypes.c_int64, ctypes.c_int64, ctypes.c_int, ctypes.c_int,
-                            ctypes.c_double, ctypes.c_int64, ctypes.c_double, ctypes.c_int] + \
+                            ctypes.c_double, ctypes.c_int64, ctypes.c_double] + \
         [ctypes.c_void_p] * 3
 
-    def run(n, ntrees, bit, canon, budget, cap=0, share=0.7, split=False):
+    def run(n, ntrees, bit, canon, budget, cap=0, share=0.7):
         bw, bt, b = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_uint64()
-        lib.hp_plan(n, ntrees, int(bit), int(canon), float(budget), cap, share, int(split),
-                    ctypes.byref(bw), ctypes.byref(bt), ctypes.byref(b))
+        lib.hp_plan(n, ntrees, int(bit), int(canon), float(budget), cap, share, ctypes.byref(bw),
+                    ctypes.byref(bt), ctypes.byref(b))
         return bw.value, bt.value, b.value
     return run
 
@@ -53,20 +53,19 @@ def plan(tmp_path_factory):
 SLACK = 256 * 12  # at most 12 aligned regions
 
 
-@pytest.mark.parametrize("split", [False, True])
 @pytest.mark.parametrize("share", [0.7, 0.9])
 @pytest.mark.parametrize("bit", [False, True])
 @pytest.mark.parametrize("canon", [False, True])
 @pytest.mark.parametrize("n", [2, 2000, 10 ** 6, 4 * 10 ** 6])
-def test_plans_fit_the_budget(plan, n, bit, canon, share, split):
+def test_plans_fit_the_budget(plan, n, bit, canon, share):
     one = plan(n, 1, bit, canon, 0.0)[2]  # what a single tree needs
     for budget in (one, 3.7 * one, 1e9, 4e10, 2.3e11):
         for ntrees in (1, 64, 10000):
-            bw, bt, b = plan(n, ntrees, bit, canon, budget, share=share, split=split)
+            bw, bt, b = plan(n, ntrees, bit, canon, budget, share=share)
             assert 1 <= bt <= bw <= min(ntrees, 1 << 20) and bt <= 65535
             if budget >= one:
                 assert b <= budget + SLACK, (budget, bw, bt, b)
-            if not bit and not split:
+            if not bit:
                 assert bt == min(bw, 65535)
 
 
@@ -85,7 +84,3 @@ def test_caps_and_monotone_budget(plan):
     assert 0.68 < walk / 1e11 <= 0.7
     bw, bt, b = plan(n, 10 ** 6, True, False, 2.2e11, share=0.9)
     assert 0.88 < bw * 12 * n / 2.2e11 <= 0.9 and bt >= 1
-    # shallow graphs with the split: the walk's share, and more walk trees
-    bw2, bt2, _ = plan(n, 10 ** 6, False, False, 2.2e11, split=True)
-    assert 0.68 < bw2 * 12 * n / 2.2e11 <= 0.7 and bt2 < bw2
-    assert bw2 > plan(n, 10 ** 6, False, False, 2.2e11)[0]
