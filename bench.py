@@ -720,8 +720,9 @@ def serve_leg(args, kc):
 # captures (dram__bytes_read.sum + dram__bytes_write.sum) on the 300x300
 # perturbed grid with 1000 trees in flight (profiles/); a full-size launch runs
 # for seconds, too long to capture, so its traffic is this figure times its
-# departures.  k_wilson_warp: 10.213 GB for 1,133,364,358 departures.
-WALKER_GRID_DRAM_BYTES_PER_STEP = {"warp": 10.213e9 / 1133364358}
+# departures.  k_wilson_warp: 10.213 GB, k_wilson: 4.648 GB, each for the
+# same 1,133,364,358 departures.
+WALKER_GRID_DRAM_BYTES_PER_STEP = {"warp": 10.213e9 / 1133364358, "lane": 4.648e9 / 1133364358}
 
 
 def main():
