@@ -187,6 +187,7 @@ struct TransformIn {
     const int32_t *din;       // [B][n] DFN of the old tree
     const int32_t *size;      // [B][n]
     const int32_t *pre;       // [B][n] preorder -> vertex
+    int32_t *scratch;         // [B][>= n] int32 per tree (cut-link's per-position counts)
     const int64_t *slot;      // [B] pool index of each tree
     int32_t *pool_parents;    // [P][n] written in place
     double *factor;           // [B] d_old / d_new
@@ -290,13 +291,17 @@ __global__ void __launch_bounds__(128) k_cut_link(TransformIn a, int64_t B) {
     const int32_t c = (w_next(wd[a.u]) == a.v) ? a.u : a.v;
     const int32_t qv = (c == a.u) ? a.v : a.u;
     const int32_t lo = din[c], hi = din[c] + sz[c] - 1;
-    // count crossing edges (G' no longer has e)
+    // count crossing edges (G' no longer has e) from the smaller side of the
+    // cut: the preorder positions of Sub(tau, c), or all the others
+    const bool inside = 2 * (int64_t)sz[c] <= n;
+    const int64_t span = inside ? (int64_t)sz[c] : n - sz[c];
     long long cross = 0;
-    for (int64_t q = lo + lane; q <= hi; q += 32) {
+    for (int64_t kq = lane; kq < span; kq += 32) {
+        const int64_t q = inside ? lo + kq : (kq < lo ? kq : kq + sz[c]);
         const int32_t y = pre[q];
         for (int64_t e = a.row_off[y]; e < a.row_off[y + 1]; ++e) {
             const int32_t dz = din[a.col[e]];
-            if (dz < lo || dz > hi) ++cross;
+            if ((dz >= lo && dz <= hi) != inside) ++cross;
         }
     }
 #pragma unroll
@@ -310,10 +315,60 @@ __global__ void __launch_bounds__(128) k_cut_link(TransformIn a, int64_t B) {
         k = (long long)bounded_draw(a.seed, a.seq, (uint32_t)a.slot[t], 0, kTagCutLink,
                                     (uint32_t)cross);
     k = __shfl_sync(kFull, k, 0);
-    // find the k-th crossing edge in (preorder position, neighbour) order
+    // find the k-th crossing edge in (preorder position of the inside end,
+    // outside end ascending) order
     int32_t ia = -1, ob = -1;
     long long before = 0;
-    for (int64_t base = lo; base <= hi; base += 32) {
+    if (!inside) {
+        // the outside is smaller: tally each inside position's crossing edges
+        // from the outside (atomics in L2), then scan the tallies in order
+        int32_t *cnt = a.scratch + t * n;
+        for (int64_t i = lane; i < sz[c]; i += 32) __stcg(cnt + i, 0);
+        __threadfence_block();
+        __syncwarp();
+        for (int64_t kq = lane; kq < span; kq += 32) {
+            const int64_t q = kq < lo ? kq : kq + sz[c];
+            const int32_t y = pre[q];
+            for (int64_t e = a.row_off[y]; e < a.row_off[y + 1]; ++e) {
+                const int32_t dz = din[a.col[e]];
+                if (dz >= lo && dz <= hi) atomicAdd(cnt + (dz - lo), 1);
+            }
+        }
+        __threadfence_block();
+        __syncwarp();
+        int64_t hit = -1;  // inside position (from lo) holding the k-th edge
+        long long hit_start = 0;
+        for (int64_t base = 0; base < sz[c] && hit < 0; base += 32) {
+            const int64_t i = base + lane;
+            const long long mine = i < sz[c] ? (long long)__ldcg(cnt + i) : 0;
+            long long incl = mine;
+#pragma unroll
+            for (int s2 = 1; s2 < 32; s2 <<= 1) {
+                const long long yv = __shfl_up_sync(kFull, incl, s2);
+                if (lane >= s2) incl += yv;
+            }
+            const long long start = before + incl - mine;
+            const unsigned hb = __ballot_sync(kFull, mine > 0 && k >= start && k < start + mine);
+            if (hb) {
+                const int src = __ffs(hb) - 1;
+                hit = base + src;
+                hit_start = __shfl_sync(kFull, start, src);
+            }
+            before += __shfl_sync(kFull, incl, 31);
+        }
+        if (lane == 0 && hit >= 0) {
+            const int32_t y = pre[lo + hit];
+            long long idx = hit_start;
+            for (int64_t e = a.row_off[y]; e < a.row_off[y + 1]; ++e) {
+                const int32_t z = a.col[e];
+                const int32_t dz = din[z];
+                if (dz >= lo && dz <= hi) continue;
+                if (idx == k) { ia = y; ob = z; break; }
+                ++idx;
+            }
+        }
+    }
+    for (int64_t base = lo; inside && base <= hi; base += 32) {
         const int64_t q = base + lane;
         int32_t y = -1;
         long long mine = 0;
@@ -484,6 +539,7 @@ cudaError_t launch_link_cut(const int64_t *row_off, const int32_t *col, WaveView
     a.din = w.din;
     a.size = w.size;
     a.pre = w.aux;
+    a.scratch = reinterpret_cast<int32_t *>(w.vol);  // 8n bytes per tree, unused here
     a.slot = slot;
     a.pool_parents = pool_parents;
     a.factor = factor;
