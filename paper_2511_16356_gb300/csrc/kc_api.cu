@@ -1253,14 +1253,7 @@ void run_wave_reject(kc_graph *g, Plan &p, int64_t B, int64_t sid0) {
 void do_sample_reject(kc_graph *g, int64_t ntrees) {
     const double hint = g->cfg.reject_accept_hint > 0 ? g->cfg.reject_accept_hint : 8.0 / 9.0;
     auto wave_size = [&](int64_t need) {
-        const double rate = g->rej_drawn > 0
-                                ? std::max(1.0 / 64.0, (double)(g->rej_accepted + 1) /
-                                                           (double)(g->rej_drawn + 1))
-                                : hint;
-        // expected draws plus three standard deviations of the accepted count
-        const double want = (double)need / rate;
-        const double sd = std::sqrt(want * rate * (1.0 - rate)) / rate;
-        return (int64_t)std::ceil(want + 3.0 * sd) + 8;
+        return kc_host::reject_wave_size(need, g->rej_drawn, g->rej_accepted, hint);
     };
     ensure_pool(g, g->pool + ntrees);
     // the wave's accepted trees stream through traversal chunks, so the walk

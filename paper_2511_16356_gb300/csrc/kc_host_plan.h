@@ -85,4 +85,17 @@ inline Plan plan_waves(int64_t n_vertices, int64_t ntrees, bool bit, bool canon,
     return p;
 }
 
+// Trees a rejection wave draws so that it accepts `need` trees: need / rate
+// plus three standard deviations of the accepted count, rate being the
+// acceptance rate seen on the handle so far ((accepted + 1) / (drawn + 1),
+// at least 1/64), or `hint` before any tree is seen.
+inline int64_t reject_wave_size(int64_t need, int64_t drawn, int64_t accepted, double hint) {
+    const double rate = drawn > 0 ? std::max(1.0 / 64.0, (double)(accepted + 1) /
+                                                             (double)(drawn + 1))
+                                  : hint;
+    const double want = (double)need / rate;
+    const double sd = std::sqrt(want * rate * (1.0 - rate)) / rate;
+    return (int64_t)std::ceil(want + 3.0 * sd) + 8;
+}
+
 }  // namespace kc_host

@@ -24,6 +24,9 @@ extern "C" void hp_plan(int64_t n, int64_t ntrees, int bit, int canon, double bu
     *bt = p.BT;
     *bytes = kc_host::ws_bytes(n, p);
 }
+extern "C" int64_t hp_reject(int64_t need, int64_t drawn, int64_t accepted, double hint) {
+    return kc_host::reject_wave_size(need, drawn, accepted, hint);
+}
 """
 
 
@@ -47,6 +50,9 @@ def plan(tmp_path_factory):
         lib.hp_plan(n, ntrees, int(bit), int(canon), float(budget), cap, share, ctypes.byref(bw),
                     ctypes.byref(bt), ctypes.byref(b))
         return bw.value, bt.value, b.value
+    lib.hp_reject.restype = ctypes.c_int64
+    lib.hp_reject.argtypes = [ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_double]
+    run.reject = lib.hp_reject
     return run
 
 
@@ -84,3 +90,25 @@ def test_caps_and_monotone_budget(plan):
     assert 0.68 < walk / 1e11 <= 0.7
     bw, bt, b = plan(n, 10 ** 6, True, False, 2.2e11, share=0.9)
     assert 0.88 < bw * 12 * n / 2.2e11 <= 0.9 and bt >= 1
+
+
+def test_rejection_wave_size_rarely_falls_short(plan):
+    """A rejection wave draws need / rate plus three standard deviations: at the
+    assumed rate the chance that it accepts fewer than `need` trees is about
+    the normal tail beyond 3 sd (checked by binomial sampling), it grows as the
+    rate falls, uses the hint before any tree is seen, and the observed rate
+    afterwards."""
+    import numpy as np
+
+    rs = plan.reject
+    rng = np.random.default_rng(0)
+    for rate in (0.9, 0.65, 0.3):
+        for need in (100, 4096, 10000):
+            B = rs(need, 0, 0, rate)
+            assert B >= need / rate
+            short = (rng.binomial(B, rate, size=20000) < need).mean()
+            assert short < 0.005, (rate, need, B, short)
+    assert rs(10000, 0, 0, 0.5) > rs(10000, 0, 0, 0.8)
+    # the observed rate replaces the hint
+    assert rs(10000, 20000, 10000, 0.9) == rs(10000, 0, 0, 10001 / 20001)
+    assert rs(10000, 1000, 0, 0.9) == rs(10000, 0, 0, 1 / 64)  # floor on the rate
