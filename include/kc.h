@@ -162,6 +162,19 @@ typedef struct {
                                    handle's first rejection wave so that it usually
                                    accepts enough trees in one go; later waves use the
                                    share seen so far.  0: 8/9                       */
+    int32_t ttf_segments;       /* BIT evaluation of f (Algorithm 1) split into preorder
+                                   segments, each replayed by its own warp from the
+                                   DFS state rebuilt at its first position (same f,
+                                   exactly).  0: automatic -- the chunks evaluated
+                                   after their wave's walk has ended, up to 16
+                                   segments a tree and about 32 segment warps an SM,
+                                   in memory the wave no longer needs (sub-wave slots
+                                   the chunk leaves free, the stack buffer, rejected
+                                   trees' walk arrays); 1: never; k >= 2
+                                   (at most 64): up to k segments for every BIT
+                                   evaluation, with a handle buffer for what free
+                                   memory does not hold                             */
+    int32_t reserved2;
 } kc_config;
 
 /* Fill *cfg with the defaults listed above. */

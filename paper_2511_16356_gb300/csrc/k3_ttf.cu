@@ -98,15 +98,34 @@ __device__ __forceinline__ void bit_range_add(int64_t *bit, int64_t n, int lane,
     if ((int64_t)r + 2 <= n) bit_point_add(bit, n, lane, (int64_t)r + 2, -val);
 }
 
-template <bool kMulti>
-__global__ void __launch_bounds__(128) k_ttf_bit(GraphView g_in, WaveView w_in, MultiSub ms) {
+// Range add of tau-ancestor x (x != r, tau parent par) in Algorithm 1: kind 1
+// when p(x) = p0(x) (tau0-subtree of x, value 2m - vol(x)), kind 2 when
+// p0(p(x)) = x (tau0-subtree of p(x), value vol(x) - 2m), 0 otherwise.
+__device__ __forceinline__ int ttf_entry(const GraphView &g, int32_t x, int32_t par, int32_t r,
+                                         int32_t twom, int64_t volx, int32_t &el, int32_t &er,
+                                         int32_t &eval) {
+    const int32_t vv = (int32_t)volx;
+    if (g.p0[x] == par) {
+        el = g.in0[x]; er = g.out0[x]; eval = twom - vv;
+        return 1;
+    }
+    if (par != r && g.p0[par] == x) {
+        el = g.in0[par]; er = g.out0[par]; eval = vv - twom;
+        return 2;
+    }
+    return 0;
+}
+
+// One warp replays the preorder positions [lo, hi) of sub-wave tree t
+// (Algorithm 1) on the Fenwick array `bit` (1-based) and the memory stack `stk`
+// (sp entries on entry, the deepest on top); returns this lane's share of the
+// sum of d(v) Q(v) over those positions.  ok = false on a stack overflow (the
+// error bit is set).
+__device__ __forceinline__ long long ttf_bit_sweep(const GraphView &g, const WaveView &w,
+                                                   int64_t t, int64_t *bit, int4 *stk,
+                                                   int64_t lo, int64_t hi, int64_t sp,
+                                                   bool &ok) {
     const int lane = threadIdx.x & 31;
-    GraphView g;
-    WaveView w;
-    int64_t t;
-    if (!pick_tree<kMulti>(ms, g_in, w_in, ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5,
-                           g, w, t))
-        return;
     const int64_t n = g.n;
     const int32_t r = g.root;
     const int32_t twom = (int32_t)g.twom;  // host guarantees 2m < 2^31 for this kernel
@@ -114,15 +133,13 @@ __global__ void __launch_bounds__(128) k_ttf_bit(GraphView g_in, WaveView w_in, 
     const int32_t *__restrict__ size = w.size + t * n;
     const int64_t *__restrict__ vol = w.vol + t * n;
     const int32_t *__restrict__ pre = w.aux + t * n;
-    int64_t *bit = w.bit + t * (n + 1);  // zeroed, 1-based
-    int4 *stk = reinterpret_cast<int4 *>(w.stack) + t * w.stack_cap;
     const unsigned lt_mask = (1u << lane) - 1u;
+    ok = true;
 
-    int64_t sp = 0;         // entries in the memory stack
     long long facc = 0;     // this lane's share of f
-    for (int64_t base = 0; base < n; base += 32) {
+    for (int64_t base = lo; base < hi; base += 32) {
         const int64_t i = base + lane;
-        const bool act = i < n;
+        const bool act = i < hi;
         // ---- per-vertex data for preorder position i
         int32_t v = -1, kind = 0, el = 0, er = 0, eval = 0, eout = 0, qpos = 0, dv = 0;
         if (act) {
@@ -135,14 +152,7 @@ __global__ void __launch_bounds__(128) k_ttf_bit(GraphView g_in, WaveView w_in, 
             qpos = g.in0[v];
             dv = g.deg[v];
             eout = (int32_t)i + size[v] - 1;
-            if (v != r) {
-                const int32_t vv = (int32_t)vol[v];
-                if (g.p0[v] == par) {
-                    kind = 1; el = qpos; er = g.out0[v]; eval = twom - vv;
-                } else if (par != r && g.p0[par] == v) {
-                    kind = 2; el = g.in0[par]; er = g.out0[par]; eval = vv - twom;
-                }
-            }
+            if (v != r) kind = ttf_entry(g, v, par, r, twom, vol[v], el, er, eval);
         }
         // ---- prefix sums at the start of the chunk
         long long pf = 0;
@@ -164,7 +174,7 @@ __global__ void __launch_bounds__(128) k_ttf_bit(GraphView g_in, WaveView w_in, 
         __syncwarp();
         for (int j = 0; j < 32; ++j) {
             const int64_t ij = base + j;
-            if (ij >= n) break;
+            if (ij >= hi) break;
             // pop every stacked ancestor whose subtree ended before position ij
             while (true) {
                 int32_t pl, pr, pv;
@@ -216,14 +226,124 @@ __global__ void __launch_bounds__(128) k_ttf_bit(GraphView g_in, WaveView w_in, 
         sp = nsp + __popc(cmask);
         if (sp > w.stack_cap) {
             if (lane == 0) atomicOr(w.err, kErrBadTree);
-            return;
+            ok = false;
+            return 0;
         }
         __threadfence_block();
         __syncwarp();
     }
+    return facc;
+}
+
+template <bool kMulti>
+__global__ void __launch_bounds__(128) k_ttf_bit(GraphView g_in, WaveView w_in, MultiSub ms) {
+    const int lane = threadIdx.x & 31;
+    GraphView g;
+    WaveView w;
+    int64_t t;
+    if (!pick_tree<kMulti>(ms, g_in, w_in, ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5,
+                           g, w, t))
+        return;
+    const int64_t n = g.n;
+    int64_t *bit = w.bit + t * (n + 1);  // zeroed, 1-based
+    int4 *stk = reinterpret_cast<int4 *>(w.stack) + t * w.stack_cap;
+    bool ok;
+    long long facc = ttf_bit_sweep(g, w, t, bit, stk, 0, n, 0, ok);
+    if (!ok) return;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) facc += __shfl_down_sync(kFull, facc, o);
     if (lane == 0) w.f[wave_tree(w, t)] = facc;
+}
+
+// Algorithm 1 over one preorder segment [lo, hi) of a tree per warp.  At
+// position lo the DFS stack holds the strict tau-ancestors of u = pre[lo] that
+// add a range, and the Fenwick array holds the sum of their range adds (every
+// ancestor of a later position that precedes lo is an ancestor of u; entries
+// pushed and popped before lo cancel).  Lane 0 collects them walking up the
+// tau parents (deepest first), the warp reverses them into stack order (root
+// side at the bottom) and replays their range adds, then sweeps the segment;
+// its share of f is added to the tree's f, which the caller zeroed.
+__global__ void __launch_bounds__(128) k_ttf_bit_seg(GraphView g, WaveView w,
+                                                     const TtfSeg *__restrict__ segs,
+                                                     int64_t nseg) {
+    const int lane = threadIdx.x & 31;
+    const int64_t si = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (si >= nseg) return;
+    const TtfSeg sg = segs[si];
+    const int64_t n = g.n;
+    const int32_t r = g.root;
+    const int32_t twom = (int32_t)g.twom;
+    const int64_t t = sg.t;
+    const uint64_t *__restrict__ word = w.word + wave_tree(w, t) * n;
+    const int32_t *__restrict__ size = w.size + t * n;
+    const int64_t *__restrict__ vol = w.vol + t * n;
+    const int32_t *__restrict__ din = w.din + t * n;
+    const int32_t *__restrict__ pre = w.aux + t * n;
+    int4 *stk = sg.stk;
+    int64_t sp = 0;
+    if (sg.lo > 0) {
+        long long cnt = 0;
+        if (lane == 0) {
+            const int32_t u = pre[sg.lo];
+            int32_t x = (u >= 0 && u < n) ? w_next(word[u]) : -1;
+            if (u < 0 || u >= n) cnt = -1;
+            int64_t hops = 0;
+            while (cnt >= 0 && x != r) {
+                if (x < 0 || x >= n || ++hops > n) {
+                    cnt = -1;
+                    break;
+                }
+                const int32_t par = w_next(word[x]);
+                if (par < 0 || par >= n) {  // only the root has no parent
+                    cnt = -1;
+                    break;
+                }
+                int32_t el = 0, er = 0, eval = 0;
+                if (ttf_entry(g, x, par, r, twom, vol[x], el, er, eval)) {
+                    if (cnt >= w.stack_cap) {
+                        cnt = -1;
+                        break;
+                    }
+                    stk[cnt++] = make_int4(din[x] + size[x] - 1, el, er, eval);
+                }
+                x = par;
+            }
+            if (cnt < 0) atomicOr(w.err, kErrBadTree);
+        }
+        cnt = __shfl_sync(kFull, cnt, 0);
+        if (cnt < 0) return;
+        __syncwarp();
+        for (long long e = lane; e < cnt / 2; e += 32) {
+            const int4 a = stk[e], b = stk[cnt - 1 - e];
+            stk[e] = b;
+            stk[cnt - 1 - e] = a;
+        }
+        __syncwarp();
+        for (long long e = 0; e < cnt; ++e) {
+            const int4 en = stk[e];
+            bit_range_add(sg.bit, n, lane, en.y, en.z, (long long)en.w);
+        }
+        __threadfence_block();
+        __syncwarp();
+        sp = cnt;
+    }
+    bool ok;
+    long long facc = ttf_bit_sweep(g, w, t, sg.bit, stk, sg.lo, sg.hi, sp, ok);
+    if (!ok) return;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) facc += __shfl_down_sync(kFull, facc, o);
+    if (lane == 0 && facc != 0)
+        atomicAdd((unsigned long long *)(w.f + wave_tree(w, t)), (unsigned long long)facc);
+}
+
+// zero entries 1 .. n of every segment's Fenwick array
+__global__ void k_zero_seg_bits(const TtfSeg *__restrict__ segs, int64_t nseg, int64_t n) {
+    for (int64_t s = blockIdx.y; s < nseg; s += gridDim.y) {
+        int64_t *b = segs[s].bit;
+        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+             i += (int64_t)gridDim.x * blockDim.x)
+            b[i + 1] = 0;
+    }
 }
 
 }  // namespace
@@ -235,6 +355,16 @@ cudaError_t launch_ttf_scan(const GraphView &g, WaveView w, cudaStream_t s) {
     }
     dim3 grid((unsigned)((g.n + 255) / 256), (unsigned)w.B);
     k_ttf_scan<false><<<grid, 256, 0, s>>>(g, w, MultiSub{});
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ttf_bit_seg(const GraphView &g, WaveView w, const TtfSeg *segs, int64_t nseg,
+                              cudaStream_t s) {
+    if (nseg <= 0) return cudaSuccess;
+    const dim3 zgrid((unsigned)std::min<int64_t>((g.n + 255) / 256, 64),
+                     (unsigned)std::min<int64_t>(nseg, 65535));
+    k_zero_seg_bits<<<zgrid, 256, 0, s>>>(segs, nseg, g.n);
+    k_ttf_bit_seg<<<(unsigned)((nseg * 32 + 127) / 128), 128, 0, s>>>(g, w, segs, nseg);
     return cudaGetLastError();
 }
 

@@ -231,6 +231,157 @@ void ensure_stack(kc_graph *g, Plan &p, uint32_t maxdepth, cudaStream_t st = nul
     p.stack_cap = need_cap;
 }
 
+// Segmented BIT evaluation of f (k_ttf_bit_seg) -------------------------------
+
+// Device memory that a segmented evaluation may take its segments' Fenwick
+// arrays and stacks from.
+struct SegRegion {
+    char *p;
+    size_t bytes;
+};
+
+// The most segments per tree cfg.ttf_segments allows for a chunk of b trees:
+// forced k (>= 2), never (1), or automatic (0) -- only for chunks evaluated
+// after their wave's walk has ended (split while the walk runs, a chunk's
+// warps slow the walker down), about 32 segment warps an SM (the residency of
+// k_ttf_bit_seg), at most 16 segments a tree; the memory the chunk may use
+// bounds it further.
+int seg_limit(const kc_graph *g, int64_t b, bool walk_over) {
+    const int cfgk = g->cfg.ttf_segments;
+    if (cfgk >= 2) return cfgk;
+    if (cfgk == 1 || !walk_over || b <= 0) return 0;
+    const int64_t k = std::max<int64_t>(32, 32 * g->num_sms) / b;
+    return (int)std::min<int64_t>(16, k);
+}
+
+// Segment tables for a wave of B trees: staging and device copies of
+// B * max(16, cfg.ttf_segments) entries, taken from the start.
+void reset_segtab(kc_graph *g, int64_t B) {
+    const int64_t cap = B * std::max(16, g->cfg.ttf_segments);
+    g->seg_used = 0;
+    if (cap <= g->segtab_cap) return;
+    // both streams are idle between waves: nothing reads the old tables
+    KC_CK(g, cudaStreamSynchronize(g->stream));
+    if (g->stream2) KC_CK(g, cudaStreamSynchronize(g->stream2));
+    if (g->h_segtab) cudaFreeHost(g->h_segtab);
+    g->h_segtab = nullptr;
+    dfree(g->d_segtab);
+    g->d_segtab = nullptr;
+    g->segtab_cap = 0;
+    KC_CK(g, cudaMallocHost((void **)&g->h_segtab, sizeof(TtfSeg) * (size_t)cap));
+    dalloc(g, &g->d_segtab, (size_t)cap);
+    g->segtab_cap = cap;
+}
+
+// f of the b = sv.B trees of a sub-wave from k preorder segments per tree,
+// k the largest value <= kmax for which b k Fenwick arrays (n int64, 8-byte
+// aligned) and then b k stacks (stack_cap int4, 16-byte aligned) fit in
+// `regions`; with grow (cfg.ttf_segments >= 2) the handle buffer d_segx holds
+// kmax when they do not.  Segment j of a tree covers positions
+// [j n / k, (j + 1) n / k).  Uploads the table and launches the segmented
+// kernels on s; the caller has zeroed the trees' f.  Returns k, or 0 when fewer
+// than two segments fit (the caller then runs the one-warp-per-tree kernel).
+int ttf_bit_segmented(kc_graph *g, const GraphView &gv, const WaveView &sv, int kmax,
+                      std::vector<SegRegion> regions, bool grow, cudaStream_t s) {
+    const int64_t b = sv.B, n = g->n;
+    if (kmax < 2 || b <= 0) return 0;
+    const size_t bit_bytes = sizeof(int64_t) * (size_t)n;
+    const size_t stk_bytes = sizeof(int4) * (size_t)sv.stack_cap;
+    std::vector<int64_t *> bits;
+    std::vector<int4 *> stks;
+    auto fit = [&](int k) {
+        const size_t need = (size_t)(b * k);
+        bits.clear();
+        stks.clear();
+        std::vector<uintptr_t> next(regions.size());
+        for (size_t i = 0; i < regions.size(); ++i) {
+            const uintptr_t e = (uintptr_t)regions[i].p + regions[i].bytes;
+            uintptr_t a = ((uintptr_t)regions[i].p + 7) & ~(uintptr_t)7;
+            while (bits.size() < need && a + bit_bytes <= e) {
+                bits.push_back((int64_t *)(a - sizeof(int64_t)));  // 1-based base
+                a += bit_bytes;
+            }
+            next[i] = a;
+        }
+        if (bits.size() < need) return false;
+        for (size_t i = 0; i < regions.size() && stks.size() < need; ++i) {
+            const uintptr_t e = (uintptr_t)regions[i].p + regions[i].bytes;
+            uintptr_t a = (next[i] + 15) & ~(uintptr_t)15;
+            while (stks.size() < need && a + stk_bytes <= e) {
+                stks.push_back((int4 *)a);
+                a += stk_bytes;
+            }
+        }
+        return stks.size() >= need;
+    };
+    int k = kmax;
+    while (k >= 2 && !fit(k)) --k;
+    if (k < kmax && grow) {
+        const size_t want = (size_t)(b * kmax) * (bit_bytes + stk_bytes) + 64;
+        if (want > g->segx_bytes) {
+            if (g->d_segx) KC_CK(g, cudaFreeAsync(g->d_segx, s));
+            g->d_segx = nullptr;
+            g->segx_bytes = 0;
+            KC_CK(g, cudaMallocAsync((void **)&g->d_segx, want, s));
+            g->segx_bytes = want;
+        }
+        regions.assign(1, SegRegion{g->d_segx, g->segx_bytes});
+        k = kmax;
+        if (!fit(k)) {
+            g->last_error = "segmented BIT evaluation: buffer sizing";
+            throw Fail{KC_ERR_CUDA};
+        }
+    }
+    if (k < 2) return 0;
+    if (g->seg_used + b * k > g->segtab_cap) {
+        g->last_error = "segmented BIT evaluation: segment table overflow";
+        throw Fail{KC_ERR_CUDA};
+    }
+    TtfSeg *h = g->h_segtab + g->seg_used;
+    int64_t nseg = 0;
+    for (int64_t t = 0; t < b; ++t)
+        for (int j = 0; j < k; ++j) {
+            const int64_t lo = j * n / k, hi = (j + 1) * n / k;
+            if (lo == hi) continue;
+            const size_t q = (size_t)(t * k + j);
+            h[nseg++] = TtfSeg{bits[q], stks[q], (int32_t)t, (int32_t)lo, (int32_t)hi, 0};
+        }
+    TtfSeg *d = g->d_segtab + g->seg_used;
+    g->seg_used += nseg;
+    KC_CK(g, cudaMemcpyAsync(d, h, sizeof(TtfSeg) * (size_t)nseg, cudaMemcpyHostToDevice, s));
+    KC_CK(g, launch_ttf_bit_seg(gv, sv, d, nseg, s));
+    return k;
+}
+
+// Regions every BIT evaluation of a carved wave may reuse: the sub-wave
+// Fenwick arrays (BT trees) and the stack buffer.  Only one chunk is evaluated
+// at a time (one stream), so the next chunk finds them free again.
+std::vector<SegRegion> subwave_regions(const kc_graph *g, const Plan &p, const WaveView &w) {
+    std::vector<SegRegion> r;
+    if (w.bit) r.push_back({(char *)w.bit, sizeof(int64_t) * (size_t)(g->n + 1) * (size_t)p.BT});
+    if (g->d_stack) r.push_back({(char *)g->d_stack, g->stack_bytes});
+    return r;
+}
+
+// BIT evaluation of a chunk: segmented when seg_limit allows and memory holds
+// two or more segments a tree, else one warp per tree.  `walk_over`: the wave's
+// walk has ended (its rejected trees' arrays, listed in `spare`, are free).
+// Returns the kernels launched.
+int eval_ttf_bit(kc_graph *g, const GraphView &gv, const Plan &p, const WaveView &sv,
+                 bool walk_over, const std::vector<SegRegion> &spare, cudaStream_t s) {
+    const int kmax = seg_limit(g, sv.B, walk_over);
+    if (kmax >= 2) {
+        std::vector<SegRegion> regs = subwave_regions(g, p, sv);
+        if (walk_over) regs.insert(regs.end(), spare.begin(), spare.end());
+        if (!sv.tmap)  // the segments add into f
+            KC_CK(g, cudaMemsetAsync(sv.f, 0, sizeof(int64_t) * (size_t)sv.B, s));
+        if (ttf_bit_segmented(g, gv, sv, kmax, std::move(regs), g->cfg.ttf_segments >= 2, s))
+            return 2;
+    }
+    KC_CK(g, launch_ttf_bit(gv, sv, s));
+    return 1;
+}
+
 // Cap on Wilson departures (per tree for the one-walker kernel, per walker for
 // the 32-walker kernel): the configured value, or max(2^22, 1024 n) (about 60
 // times the mean step count of a road-shaped graph, far above that of
@@ -283,6 +434,9 @@ void ensure_pipeline(kc_graph *g, int64_t B) {
     if (B <= g->done_cap) return;
     if (g->h_done) cudaFreeHost(g->h_done);
     if (g->h_map) cudaFreeHost(g->h_map);
+    if (g->h_segtab) cudaFreeHost(g->h_segtab);
+    dfree(g->d_segtab);
+    dfree(g->d_segx);
     dfree(g->d_map);
     g->h_done = g->h_map = g->d_done = nullptr;
     g->done_cap = 0;
@@ -322,6 +476,8 @@ void run_wave_pipelined(kc_graph *g, Plan &p, int64_t B, int64_t sid0, bool reje
     } guard{evs};
     volatile int32_t *hd = g->h_done;
     for (int64_t t = 0; t < B; ++t) hd[t] = 0;
+    reset_segtab(g, B);
+    std::vector<SegRegion> spare;  // walk arrays of rejected trees (free once the walk ended)
     KC_CK(g, cudaMemsetAsync(g->d_err, 0, 2 * sizeof(uint32_t), s1));
     KC_CK(g, cudaMemsetAsync(w.f, 0, sizeof(int64_t) * (size_t)B, s1));
     KC_CK(g, launch_iota(c.sids, sid0, B, s1));
@@ -365,9 +521,15 @@ void run_wave_pipelined(kc_graph *g, Plan &p, int64_t B, int64_t sid0, bool reje
         for (size_t i = 0; i < unseen.size(); ++i) {
             const int32_t t = unseen[i];
             const int32_t flag = hd[t];
-            if (flag > 0) ready.push_back(t);
-            else if (flag < 0) ++skipped;
-            else unseen[keep++] = t;
+            if (flag > 0) {
+                ready.push_back(t);
+            } else if (flag < 0) {
+                ++skipped;
+                spare.push_back({(char *)(w.word + (int64_t)t * g->n), sizeof(uint64_t) * (size_t)g->n});
+                spare.push_back({(char *)(w.ord + (int64_t)t * g->n), sizeof(int32_t) * (size_t)g->n});
+            } else {
+                unseen[keep++] = t;
+            }
         }
         unseen.resize(keep);
         if ((int64_t)ready.size() >= (wdone ? 1 : chunk_min)) {
@@ -394,9 +556,11 @@ void run_wave_pipelined(kc_graph *g, Plan &p, int64_t B, int64_t sid0, bool reje
             KC_CK(g, launch_traverse(gv, sv, p.bit, s2, &nl, fast_traversal(g)));
             g->t_traverse.launches += nl;
             KC_CK(g, cudaEventRecord(e3[1], s2));
-            if (p.bit) KC_CK(g, launch_ttf_bit(gv, sv, s2));
-            else KC_CK(g, launch_ttf_scan(gv, sv, s2));
-            g->t_ttf.launches += 1;
+            if (p.bit) g->t_ttf.launches += eval_ttf_bit(g, gv, p, sv, wdone, spare, s2);
+            else {
+                KC_CK(g, launch_ttf_scan(gv, sv, s2));
+                g->t_ttf.launches += 1;
+            }
             KC_CK(g, cudaEventRecord(e3[2], s2));
             chunk_ev.push_back(e3);
             processed += b;
@@ -463,6 +627,7 @@ void run_wave(kc_graph *g, Plan &p, int64_t B, int64_t sid0, bool canonical = fa
     w.B = B;
     KC_CK(g, cudaMemsetAsync(g->d_err, 0, 2 * sizeof(uint32_t), g->stream));
     KC_CK(g, launch_iota(c.sids, sid0, B, g->stream));
+    reset_segtab(g, B);
     {
         Phase ph(g, g->t_init);
         KC_CK(g, launch_wave_init(gv, w, g->stream));
@@ -506,9 +671,10 @@ void run_wave(kc_graph *g, Plan &p, int64_t B, int64_t sid0, bool canonical = fa
         }
         {
             Phase ph(g, g->t_ttf);
-            if (p.bit) KC_CK(g, launch_ttf_bit(gv, s, g->stream));
+            int nl = 1;
+            if (p.bit) nl = eval_ttf_bit(g, gv, p, s, true, {}, g->stream);
             else KC_CK(g, launch_ttf_scan(gv, s, g->stream));
-            ph.done(1);
+            ph.done(nl);
         }
     }
     KC_CK(g, copy_sync(g, hdr, g->d_err, sizeof(hdr), cudaMemcpyDeviceToHost));
@@ -1178,6 +1344,7 @@ void run_wave_reject(kc_graph *g, Plan &p, int64_t B, int64_t sid0) {
     KC_CK(g, cudaMemsetAsync(g->d_err, 0, 2 * sizeof(uint32_t), g->stream));
     KC_CK(g, cudaMemsetAsync(w.f, 0, sizeof(int64_t) * (size_t)B, g->stream));
     KC_CK(g, launch_iota(c.sids, sid0, B, g->stream));
+    reset_segtab(g, B);
     {
         Phase ph(g, g->t_init);
         KC_CK(g, launch_wave_init(gv, w, g->stream));
@@ -1208,8 +1375,15 @@ void run_wave_reject(kc_graph *g, Plan &p, int64_t B, int64_t sid0) {
     KC_CK(g, copy_sync(g, st.data(), w.steps, sizeof(int64_t) * (size_t)B,
                        cudaMemcpyDeviceToHost));
     int64_t na = 0;
-    for (int64_t t = 0; t < B; ++t)
-        if (st[(size_t)t] >= 0) g->h_map[na++] = (int32_t)t;
+    std::vector<SegRegion> spare;  // walk arrays of the rejected trees
+    for (int64_t t = 0; t < B; ++t) {
+        if (st[(size_t)t] >= 0) {
+            g->h_map[na++] = (int32_t)t;
+        } else {
+            spare.push_back({(char *)(w.word + t * g->n), sizeof(uint64_t) * (size_t)g->n});
+            spare.push_back({(char *)(w.ord + t * g->n), sizeof(int32_t) * (size_t)g->n});
+        }
+    }
     if (na == 0) return;
     KC_CK(g, cudaMemcpyAsync(g->d_map, g->h_map, sizeof(int32_t) * (size_t)na,
                              cudaMemcpyHostToDevice, g->stream));
@@ -1229,9 +1403,10 @@ void run_wave_reject(kc_graph *g, Plan &p, int64_t B, int64_t sid0) {
         }
         {
             Phase ph(g, g->t_ttf);
-            if (p.bit) KC_CK(g, launch_ttf_bit(gv, sv, g->stream));
+            int nl = 1;
+            if (p.bit) nl = eval_ttf_bit(g, gv, p, sv, true, spare, g->stream);
             else KC_CK(g, launch_ttf_scan(gv, sv, g->stream));
-            ph.done(1);
+            ph.done(nl);
         }
     }
     KC_CK(g, copy_sync(g, hdr, g->d_err, sizeof(hdr), cudaMemcpyDeviceToHost));
@@ -1676,6 +1851,9 @@ kc_status kc_graph_destroy(kc_graph *g) {
     if (g->d_scratch) cudaFree(g->d_scratch);
     if (g->h_done) cudaFreeHost(g->h_done);
     if (g->h_map) cudaFreeHost(g->h_map);
+    if (g->h_segtab) cudaFreeHost(g->h_segtab);
+    dfree(g->d_segtab);
+    dfree(g->d_segx);
     dfree(g->d_map);
     if (g->stream2) cudaStreamDestroy(g->stream2);
     if (g->ev0) cudaEventDestroy(g->ev0);
@@ -1703,6 +1881,7 @@ kc_status kc_graph_create(int64_t n, const int64_t *row_off, const int32_t *col,
     // rejection by walk length: the 32-walker kernel, static pools, and a cap a
     // tree can meet (every non-root vertex departs at least once)
     if (!(cfg.reject_accept_hint >= 0 && cfg.reject_accept_hint <= 1)) return KC_ERR_INVALID_ARG;
+    if (cfg.ttf_segments < 0 || cfg.ttf_segments > 64) return KC_ERR_INVALID_ARG;
     if (cfg.reject_steps < 0 ||
         (cfg.reject_steps > 0 &&
          (cfg.reject_steps < n - 1 || cfg.keep_trees || cfg.autotune ||
@@ -1725,6 +1904,7 @@ kc_status kc_graph_create(int64_t n, const int64_t *row_off, const int32_t *col,
             throw Fail{KC_ERR_NO_DEVICE};
         }
         g->resident_trees = (int64_t)prop.multiProcessorCount * wilson_warp_blocks_per_sm();
+        g->num_sms = prop.multiProcessorCount;
         KC_CK(g, cudaEventCreate(&g->ev0));
         KC_CK(g, cudaEventCreate(&g->ev1));
         g->n = n;

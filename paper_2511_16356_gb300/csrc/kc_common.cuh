@@ -218,6 +218,15 @@ struct WaveView {
                                     // steps); null: the identity
 };
 
+// One preorder segment of a tree for the segmented BIT evaluation of f: its
+// Fenwick array (`bit` is the 1-based base, entries 1 .. n used), its stack
+// (stack_cap int4 entries) and the positions [lo, hi) of sub-wave tree t.
+struct TtfSeg {
+    int64_t *bit;
+    int4 *stk;
+    int32_t t, lo, hi, pad;
+};
+
 // wave tree of sub-wave tree t
 __host__ __device__ __forceinline__ int64_t wave_tree(const WaveView &w, int64_t t) {
     return w.tmap ? (int64_t)w.tmap[t] : t;
@@ -270,6 +279,7 @@ struct kc_graph {
     bool tuned = false;
     double tune_ms[4] = {0, 0, 0, 0};
     int64_t resident_trees = 0;  // trees the 32-walker kernel runs at once on the device
+    int64_t num_sms = 0;
     int64_t *d_f = nullptr;
     double *d_w = nullptr;
     int64_t *d_steps = nullptr;
@@ -310,6 +320,13 @@ struct kc_graph {
     cudaStream_t stream2 = nullptr;
     int32_t *h_done = nullptr, *d_done = nullptr;  // mapped pinned host memory
     int32_t *h_map = nullptr;                      // pinned staging of tree maps
+    // segmented BIT evaluation: segment tables of the current wave (pinned
+    // staging and device copy, seg_used entries taken), and the handle buffer
+    // for segments that free memory does not hold (cfg.ttf_segments >= 2)
+    kc::TtfSeg *h_segtab = nullptr, *d_segtab = nullptr;
+    int64_t segtab_cap = 0, seg_used = 0;
+    char *d_segx = nullptr;
+    size_t segx_bytes = 0;
     int32_t *d_map = nullptr;
     int64_t done_cap = 0;
     std::string last_error;
@@ -423,6 +440,11 @@ cudaError_t launch_traverse(const GraphView &g, WaveView w, bool want_preorder, 
                             int *launches = nullptr, int mode = kTravCanonical);
 cudaError_t launch_ttf_scan(const GraphView &g, WaveView w, cudaStream_t s);
 cudaError_t launch_ttf_bit(const GraphView &g, WaveView w, cudaStream_t s);
+// f of the sub-wave's trees from segments that each start from the DFS state
+// rebuilt at their first position; zeroes the segments' Fenwick arrays first and
+// adds into w.f (zeroed by the caller).  segs: device table of nseg entries.
+cudaError_t launch_ttf_bit_seg(const GraphView &g, WaveView w, const TtfSeg *segs, int64_t nseg,
+                               cudaStream_t s);
 cudaError_t launch_pool_append(WaveView w, int64_t first, int64_t *pool_f, double *pool_w,
                                int64_t *pool_steps, int64_t *pool_sid, const int64_t *sids,
                                int32_t *pool_parents, int64_t n, cudaStream_t s);

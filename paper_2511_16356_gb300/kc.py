@@ -46,6 +46,7 @@ class kc_config(ctypes.Structure):
         ("tau0_kind", ctypes.c_int32), ("reserved1", ctypes.c_int32),
         ("tau0_seed", ctypes.c_uint64), ("reject_steps", ctypes.c_int64),
         ("reject_accept_hint", ctypes.c_double),
+        ("ttf_segments", ctypes.c_int32), ("reserved2", ctypes.c_int32),
     ]
 
 

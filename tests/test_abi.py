@@ -118,6 +118,30 @@ def test_rejection_config_is_checked_before_any_device_work(lib):
         assert status(reject_steps=100, walker=kc.KC_WALK_LANE) == "KC_ERR_NO_DEVICE"
 
 
+def test_ttf_segments_config_is_checked_before_any_device_work(lib):
+    """ttf_segments: 0 (automatic, the default), 1 (never) or 2 .. 64 segments a
+    tree; anything else is INVALID_ARG before the device is touched."""
+    from paper_2511_16356_gb300 import kc
+    from paper_2511_16356_gb300 import synth as S
+
+    g = S.cycle(12)
+
+    def status(k):
+        c = kc.kc_config_default()
+        c.ttf_segments = k
+        st, h = kc.kc_graph_create(g.row_off, g.col, c, check=False)
+        if h:
+            kc.kc_graph_destroy(h)
+        return kc.STATUS[st]
+
+    assert kc.kc_config_default().ttf_segments == 0
+    assert status(-1) == "KC_ERR_INVALID_ARG"
+    assert status(65) == "KC_ERR_INVALID_ARG"
+    if not os.path.exists("/dev/nvidia0"):
+        for k in (0, 1, 2, 64):
+            assert status(k) == "KC_ERR_NO_DEVICE"
+
+
 def test_server_config_defaults(lib):
     import ctypes
 

@@ -472,3 +472,51 @@ def test_lane_walker_pipelined_waves_bit_exact(name, trees):
     assert np.array_equal(got["sid"], np.arange(trees))
     assert np.array_equal(got["steps"], st_ref)
     assert np.array_equal(got["f"], f_ref)
+
+
+@pytest.mark.parametrize("k", [2, 3, 7, 64])
+@pytest.mark.parametrize("name", ["grid17x13", "er300", "path33", "cl3000", "K3", "P3"])
+def test_segmented_bit_evaluation_bit_exact(name, k):
+    """Algorithm 1 split into k preorder segments a tree (ttf_segments = k), each
+    warp starting from the DFS stack and Fenwick state rebuilt at its first
+    position: f equals the oracle's bit for bit.  The cases cover segments of
+    fewer than 32 positions and graphs with fewer vertices than segments."""
+    g = SMALL[name]()
+    t0 = O.tau0(g)
+    seed = 4243
+    with kc.KemenyGraph.from_graph(g, _cfg(kc.KC_TTF_BIT, ttf_segments=k)) as G:
+        G.sample(seed, 150)
+        got = G.samples()
+    f_ref, st_ref = O.sample_batch(g, t0, seed, 0, 150)
+    assert np.array_equal(got["steps"], st_ref)
+    assert np.array_equal(got["f"], f_ref)
+
+
+@pytest.mark.parametrize("k", [0, 1, 5])
+def test_segmented_bit_evaluation_in_pipelined_and_rejection_waves(k):
+    """The segmented evaluation inside the waves that use it: pipelined chunks
+    forced by a small workspace (forced k: chunks evaluated while the walk
+    runs take the handle buffer), and rejection waves whose rejected trees'
+    walk arrays hold the segments once the walk has ended (automatic, k = 0).
+    k = 1 never splits.  f and step counts equal the oracle's."""
+    g = SMALL["grid17x13"]()
+    t0 = O.tau0(g)
+    with kc.KemenyGraph.from_graph(g, _cfg(kc.KC_TTF_BIT, keep_trees=0, ttf_segments=k)) as G:
+        kc.kc_graph_set_workspace_limit(G.h, 40 * 40 * g.n + 4096)
+        G.sample(31, 120)
+        assert G.stats()["trees_in_flight"] < 120
+        got = G.samples()
+    f_ref, st_ref = O.sample_batch(g, t0, 31, 0, 120)
+    assert np.array_equal(got["steps"], st_ref)
+    assert np.array_equal(got["f"], f_ref)
+    _, s_all = O.sample_batch(g, t0, 5, 0, 1000)
+    cap = int(np.quantile(s_all, 0.6))
+    ids, f, steps = O.accepted_samples(lambda a, c: O.sample_batch(g, t0, 5, a, c), cap, 300,
+                                       block=600)
+    for wk in (kc.KC_WALK_LANE, kc.KC_WALK_WARP):
+        cfg = _cfg(kc.KC_TTF_BIT, keep_trees=0, reject_steps=cap, walker=wk, ttf_segments=k)
+        with kc.KemenyGraph.from_graph(g, cfg) as G:
+            G.sample(5, 300)
+            got = G.samples()
+        assert np.array_equal(got["sid"], ids)
+        assert np.array_equal(got["f"], f) and np.array_equal(got["steps"], steps)
