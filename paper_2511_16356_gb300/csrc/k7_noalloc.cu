@@ -100,6 +100,9 @@ extern "C" kc_status kc_wilson_noalloc(int64_t n, const int64_t *d_row_off, cons
         return KC_ERR_INVALID_ARG;
     if (n_trees == 0) return KC_OK;
     if (n > kNoAllocWords / n_trees) return KC_ERR_SCRATCH_LIMIT;
+    // the launch check below reads the thread's last error: clear one that an
+    // earlier, unrelated runtime call left pending
+    (void)cudaGetLastError();
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
         (void)cudaGetLastError();

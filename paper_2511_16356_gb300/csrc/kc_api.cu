@@ -58,9 +58,19 @@ void dalloc(kc_graph *g, T **p, size_t count) {
 
 template <class T>
 void dfree(T *&p) {
-    if (p) cudaFree((void *)p);
+    if (p && cudaFree((void *)p) != cudaSuccess) (void)cudaGetLastError();
     p = nullptr;
 }
+
+void hfree(void *p) {
+    if (p && cudaFreeHost(p) != cudaSuccess) (void)cudaGetLastError();
+}
+
+// Launch checks read the runtime's per-thread last error, so an error that an
+// earlier, unrelated runtime call left pending on the calling thread would be
+// reported as this call's failure.  Entry points that do device work clear it
+// first (a sticky error of a broken context still fails the next call).
+void clear_stale_error() { (void)cudaGetLastError(); }
 
 // A blocking copy ordered after the handle's stream: the legacy default stream
 // does not wait for non-blocking streams, so plain cudaMemcpy could read
@@ -263,7 +273,7 @@ void reset_segtab(kc_graph *g, int64_t B) {
     // both streams are idle between waves: nothing reads the old tables
     KC_CK(g, cudaStreamSynchronize(g->stream));
     if (g->stream2) KC_CK(g, cudaStreamSynchronize(g->stream2));
-    if (g->h_segtab) cudaFreeHost(g->h_segtab);
+    hfree(g->h_segtab);
     g->h_segtab = nullptr;
     dfree(g->d_segtab);
     g->d_segtab = nullptr;
@@ -432,9 +442,9 @@ int wilson_launches(const kc_graph *g) { return g->walker == KC_WALK_HYBRID ? 2 
 void ensure_pipeline(kc_graph *g, int64_t B) {
     if (!g->stream2) KC_CK(g, cudaStreamCreateWithFlags(&g->stream2, cudaStreamNonBlocking));
     if (B <= g->done_cap) return;
-    if (g->h_done) cudaFreeHost(g->h_done);
-    if (g->h_map) cudaFreeHost(g->h_map);
-    if (g->h_segtab) cudaFreeHost(g->h_segtab);
+    hfree(g->h_done);
+    hfree(g->h_map);
+    hfree(g->h_segtab);
     dfree(g->d_segtab);
     dfree(g->d_segx);
     dfree(g->d_map);
@@ -1849,9 +1859,9 @@ kc_status kc_graph_destroy(kc_graph *g) {
     dfree(g->d_sorder);
     dfree(g->d_err);
     if (g->d_scratch) cudaFree(g->d_scratch);
-    if (g->h_done) cudaFreeHost(g->h_done);
-    if (g->h_map) cudaFreeHost(g->h_map);
-    if (g->h_segtab) cudaFreeHost(g->h_segtab);
+    hfree(g->h_done);
+    hfree(g->h_map);
+    hfree(g->h_segtab);
     dfree(g->d_segtab);
     dfree(g->d_segx);
     dfree(g->d_map);
@@ -1859,6 +1869,7 @@ kc_status kc_graph_destroy(kc_graph *g) {
     if (g->ev0) cudaEventDestroy(g->ev0);
     if (g->ev1) cudaEventDestroy(g->ev1);
     delete g;
+    clear_stale_error();  // nothing the frees above report outlives this call
     return KC_OK;
 }
 
@@ -1896,6 +1907,7 @@ kc_status kc_graph_create(int64_t n, const int64_t *row_off, const int32_t *col,
     if (!g) return KC_ERR_OUT_OF_MEMORY;
     g->cfg = cfg;
     try {
+        clear_stale_error();
         KC_CK(g, cudaGetDevice(&g->device));
         cudaDeviceProp prop;
         KC_CK(g, cudaGetDeviceProperties(&prop, g->device));
@@ -2045,6 +2057,7 @@ kc_status kc_graph_set_workspace_limit(kc_graph *g, int64_t bytes) {
 kc_status kc_graph_release_workspace(kc_graph *g) {
     if (!g) return KC_ERR_INVALID_ARG;
     try {
+        clear_stale_error();
         release_ws(g);
     } catch (Fail &f) {
         return f.st;
@@ -2084,6 +2097,7 @@ kc_status kc_sample(kc_graph *g, uint64_t seed, int64_t n_trees) {
     g->seed = seed;
     g->seeded = true;
     try {
+        clear_stale_error();
         do_sample(g, n_trees);
     } catch (Fail &f) {
         g->seeded = was_seeded;
@@ -2096,6 +2110,7 @@ kc_status kc_reserve(kc_graph *g, int64_t n_trees) {
     if (!g || n_trees < 0) return KC_ERR_INVALID_ARG;
     if (n_trees == 0) return KC_OK;
     try {
+        clear_stale_error();
         ensure_pool(g, g->pool + n_trees);
         Plan p = plan_for(g, n_trees, false);
         ensure_ws(g, p);
@@ -2130,6 +2145,7 @@ kc_status kc_sample_multi(kc_graph *const *graphs, const uint64_t *seeds, const 
         graphs[i]->seeded = true;
     }
     try {
+        clear_stale_error();
         do_sample_multi(graphs, n_trees, count);
     } catch (Fail &f) {
         for (int32_t i = 0; i < count; ++i) graphs[i]->seeded = was[(size_t)i];
@@ -2146,6 +2162,7 @@ kc_status kc_estimate(kc_graph *g, double eps, double delta, double *K_out) {
     const bool was_seeded = g->seeded;
     const int64_t pool0 = g->pool;
     try {
+        clear_stale_error();
         if (eps > 0 && !g->seeded) {
             g->seed = 0;
             g->seeded = true;
@@ -2189,6 +2206,7 @@ kc_status kc_get_samples(kc_graph *g, int64_t first, int64_t count, int64_t *f, 
     if (!g || first < 0 || count < 0 || first + count > g->pool) return KC_ERR_INVALID_ARG;
     if (count == 0) return KC_OK;
     try {
+        clear_stale_error();
         if (f) KC_CK(g, cudaMemcpyAsync(f, g->d_f + first, sizeof(int64_t) * count, cudaMemcpyDeviceToHost, g->stream));
         if (weight) KC_CK(g, cudaMemcpyAsync(weight, g->d_w + first, sizeof(double) * count, cudaMemcpyDeviceToHost, g->stream));
         if (steps) KC_CK(g, cudaMemcpyAsync(steps, g->d_steps + first, sizeof(int64_t) * count, cudaMemcpyDeviceToHost, g->stream));
@@ -2204,6 +2222,7 @@ kc_status kc_get_tau0(kc_graph *g, int32_t *p0, int32_t *level, int32_t *in0, in
                       int32_t *root, int32_t *ecc) {
     if (!g) return KC_ERR_INVALID_ARG;
     try {
+        clear_stale_error();
         const size_t b = sizeof(int32_t) * (size_t)g->n;
         if (p0) KC_CK(g, cudaMemcpyAsync(p0, g->d_p0, b, cudaMemcpyDeviceToHost, g->stream));
         if (level) KC_CK(g, cudaMemcpyAsync(level, g->d_level0, b, cudaMemcpyDeviceToHost, g->stream));
@@ -2228,6 +2247,7 @@ kc_status kc_get_tree(kc_graph *g, int64_t sample, int32_t *parent, int32_t *dep
         // changed by an update): traverse its stored parent array on the
         // current graph; f and the step count are the pool's
         try {
+        clear_stale_error();
             const int64_t n = g->n;
             GraphView gv = view_of(g);
             Plan p;
@@ -2381,6 +2401,7 @@ kc_status kc_get_pool_sums(kc_graph *g, kc_pool_sums *out) {
     std::memset(out, 0, sizeof(*out));
     if (g->pool == 0) return KC_OK;
     try {
+        clear_stale_error();
         const PoolSums s = reduce_pool(g);
         out->f_sum_hi = s.f_hi;
         out->f_sum_lo = s.f_lo;
@@ -2446,6 +2467,7 @@ kc_status kc_update(kc_graph *g, const kc_edge_op *ops, int64_t n_ops, int32_t m
     if (g->pool == 0) return KC_ERR_NO_SAMPLES;
     if (n_ops == 0) return KC_OK;
     try {
+        clear_stale_error();
         const kc_status st = validate_batch(g, ops, n_ops);
         if (st != KC_OK) return st;
         KC_CK(g, cudaEventRecord(g->ev0, g->stream));

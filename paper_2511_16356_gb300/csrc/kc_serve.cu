@@ -364,6 +364,7 @@ kc_status kc_server_destroy(kc_server *s) {
     for (cudaStream_t x : s->streams) cudaStreamDestroy(x);
     if (s->dstream) cudaStreamDestroy(s->dstream);
     delete s;
+    (void)cudaGetLastError();  // nothing the teardown above reports outlives this call
     return KC_OK;
 }
 

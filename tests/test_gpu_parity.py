@@ -520,3 +520,30 @@ def test_segmented_bit_evaluation_in_pipelined_and_rejection_waves(k):
             got = G.samples()
         assert np.array_equal(got["sid"], ids)
         assert np.array_equal(got["f"], f) and np.array_equal(got["steps"], steps)
+
+
+def test_pending_runtime_error_of_the_caller_is_not_reported():
+    """An error that an unrelated runtime call left pending on the calling
+    thread (here cudaSetDevice with an ordinal that does not exist, a plain
+    argument error) is not reported as the failure of the library's next
+    call: handle creation and sampling succeed and match the oracle."""
+    import ctypes
+
+    rt = None
+    for name in ("libcudart.so.13", "/usr/local/cuda/lib64/libcudart.so.13"):
+        try:
+            rt = ctypes.CDLL(name)
+            break
+        except OSError:
+            continue
+    if rt is None:
+        pytest.skip("libcudart.so.13 not found")
+    g = SMALL["er300"]()
+    t0 = O.tau0(g)
+    assert rt.cudaSetDevice(1 << 20) != 0  # leaves an error pending on this thread
+    with kc.KemenyGraph.from_graph(g, _cfg()) as G:
+        assert rt.cudaSetDevice(1 << 20) != 0
+        G.sample(9, 40)
+        got = G.samples()
+    f_ref, _ = O.sample_batch(g, t0, 9, 0, 40)
+    assert np.array_equal(got["f"], f_ref)
