@@ -20,6 +20,7 @@
 #include "kc_host_graph.h"
 #include "kc_host_stop.h"
 #include "kc_host_plan.h"
+#include "kc_host_seg.h"
 
 namespace kc {
 cudaError_t launch_out_from_size(int64_t n, const int32_t *din, const int32_t *size,
@@ -243,12 +244,7 @@ void ensure_stack(kc_graph *g, Plan &p, uint32_t maxdepth, cudaStream_t st = nul
 
 // Segmented BIT evaluation of f (k_ttf_bit_seg) -------------------------------
 
-// Device memory that a segmented evaluation may take its segments' Fenwick
-// arrays and stacks from.
-struct SegRegion {
-    char *p;
-    size_t bytes;
-};
+using kc_host::SegRegion;
 
 // The most segments per tree cfg.ttf_segments allows for a chunk of b trees:
 // forced k (>= 2), never (1), or automatic (0) -- only for chunks evaluated
@@ -297,35 +293,8 @@ int ttf_bit_segmented(kc_graph *g, const GraphView &gv, const WaveView &sv, int 
     if (kmax < 2 || b <= 0) return 0;
     const size_t bit_bytes = sizeof(int64_t) * (size_t)n;
     const size_t stk_bytes = sizeof(int4) * (size_t)sv.stack_cap;
-    std::vector<int64_t *> bits;
-    std::vector<int4 *> stks;
-    auto fit = [&](int k) {
-        const size_t need = (size_t)(b * k);
-        bits.clear();
-        stks.clear();
-        std::vector<uintptr_t> next(regions.size());
-        for (size_t i = 0; i < regions.size(); ++i) {
-            const uintptr_t e = (uintptr_t)regions[i].p + regions[i].bytes;
-            uintptr_t a = ((uintptr_t)regions[i].p + 7) & ~(uintptr_t)7;
-            while (bits.size() < need && a + bit_bytes <= e) {
-                bits.push_back((int64_t *)(a - sizeof(int64_t)));  // 1-based base
-                a += bit_bytes;
-            }
-            next[i] = a;
-        }
-        if (bits.size() < need) return false;
-        for (size_t i = 0; i < regions.size() && stks.size() < need; ++i) {
-            const uintptr_t e = (uintptr_t)regions[i].p + regions[i].bytes;
-            uintptr_t a = (next[i] + 15) & ~(uintptr_t)15;
-            while (stks.size() < need && a + stk_bytes <= e) {
-                stks.push_back((int4 *)a);
-                a += stk_bytes;
-            }
-        }
-        return stks.size() >= need;
-    };
-    int k = kmax;
-    while (k >= 2 && !fit(k)) --k;
+    std::vector<uintptr_t> bits, stks;
+    int k = kc_host::fit_segments(regions, b, kmax, bit_bytes, stk_bytes, bits, stks);
     if (k < kmax && grow) {
         const size_t want = (size_t)(b * kmax) * (bit_bytes + stk_bytes) + 64;
         if (want > g->segx_bytes) {
@@ -335,9 +304,10 @@ int ttf_bit_segmented(kc_graph *g, const GraphView &gv, const WaveView &sv, int 
             KC_CK(g, cudaMallocAsync((void **)&g->d_segx, want, s));
             g->segx_bytes = want;
         }
-        regions.assign(1, SegRegion{g->d_segx, g->segx_bytes});
+        regions.assign(1, SegRegion{(uintptr_t)g->d_segx, g->segx_bytes});
         k = kmax;
-        if (!fit(k)) {
+        if (!kc_host::carve_segments(regions, (size_t)(b * k), bit_bytes, stk_bytes, bits,
+                                     stks)) {
             g->last_error = "segmented BIT evaluation: buffer sizing";
             throw Fail{KC_ERR_CUDA};
         }
@@ -354,7 +324,8 @@ int ttf_bit_segmented(kc_graph *g, const GraphView &gv, const WaveView &sv, int 
             const int64_t lo = j * n / k, hi = (j + 1) * n / k;
             if (lo == hi) continue;
             const size_t q = (size_t)(t * k + j);
-            h[nseg++] = TtfSeg{bits[q], stks[q], (int32_t)t, (int32_t)lo, (int32_t)hi, 0};
+            h[nseg++] = TtfSeg{(int64_t *)bits[q], (int4 *)stks[q], (int32_t)t, (int32_t)lo,
+                               (int32_t)hi, 0};
         }
     TtfSeg *d = g->d_segtab + g->seg_used;
     g->seg_used += nseg;
@@ -368,8 +339,8 @@ int ttf_bit_segmented(kc_graph *g, const GraphView &gv, const WaveView &sv, int 
 // at a time (one stream), so the next chunk finds them free again.
 std::vector<SegRegion> subwave_regions(const kc_graph *g, const Plan &p, const WaveView &w) {
     std::vector<SegRegion> r;
-    if (w.bit) r.push_back({(char *)w.bit, sizeof(int64_t) * (size_t)(g->n + 1) * (size_t)p.BT});
-    if (g->d_stack) r.push_back({(char *)g->d_stack, g->stack_bytes});
+    if (w.bit) r.push_back({(uintptr_t)w.bit, sizeof(int64_t) * (size_t)(g->n + 1) * (size_t)p.BT});
+    if (g->d_stack) r.push_back({(uintptr_t)g->d_stack, g->stack_bytes});
     return r;
 }
 
@@ -535,8 +506,8 @@ void run_wave_pipelined(kc_graph *g, Plan &p, int64_t B, int64_t sid0, bool reje
                 ready.push_back(t);
             } else if (flag < 0) {
                 ++skipped;
-                spare.push_back({(char *)(w.word + (int64_t)t * g->n), sizeof(uint64_t) * (size_t)g->n});
-                spare.push_back({(char *)(w.ord + (int64_t)t * g->n), sizeof(int32_t) * (size_t)g->n});
+                spare.push_back({(uintptr_t)(w.word + (int64_t)t * g->n), sizeof(uint64_t) * (size_t)g->n});
+                spare.push_back({(uintptr_t)(w.ord + (int64_t)t * g->n), sizeof(int32_t) * (size_t)g->n});
             } else {
                 unseen[keep++] = t;
             }
@@ -1390,8 +1361,8 @@ void run_wave_reject(kc_graph *g, Plan &p, int64_t B, int64_t sid0) {
         if (st[(size_t)t] >= 0) {
             g->h_map[na++] = (int32_t)t;
         } else {
-            spare.push_back({(char *)(w.word + t * g->n), sizeof(uint64_t) * (size_t)g->n});
-            spare.push_back({(char *)(w.ord + t * g->n), sizeof(int32_t) * (size_t)g->n});
+            spare.push_back({(uintptr_t)(w.word + t * g->n), sizeof(uint64_t) * (size_t)g->n});
+            spare.push_back({(uintptr_t)(w.ord + t * g->n), sizeof(int32_t) * (size_t)g->n});
         }
     }
     if (na == 0) return;
