@@ -246,18 +246,8 @@ void ensure_stack(kc_graph *g, Plan &p, uint32_t maxdepth, cudaStream_t st = nul
 
 using kc_host::SegRegion;
 
-// The most segments per tree cfg.ttf_segments allows for a chunk of b trees:
-// forced k (>= 2), never (1), or automatic (0) -- only for chunks evaluated
-// after their wave's walk has ended (split while the walk runs, a chunk's
-// warps slow the walker down), about 32 segment warps an SM (the residency of
-// k_ttf_bit_seg), at most 16 segments a tree; the memory the chunk may use
-// bounds it further.
 int seg_limit(const kc_graph *g, int64_t b, bool walk_over) {
-    const int cfgk = g->cfg.ttf_segments;
-    if (cfgk >= 2) return cfgk;
-    if (cfgk == 1 || !walk_over || b <= 0) return 0;
-    const int64_t k = std::max<int64_t>(32, 32 * g->num_sms) / b;
-    return (int)std::min<int64_t>(16, k);
+    return kc_host::seg_limit(g->cfg.ttf_segments, b, walk_over, g->num_sms);
 }
 
 // Segment tables for a wave of B trees: staging and device copies of

@@ -64,4 +64,18 @@ inline int fit_segments(const std::vector<SegRegion> &regions, int64_t b, int km
     return 0;
 }
 
+// The most segments per tree for a chunk of b trees under `ttf_segments`
+// (kc_config): k >= 2 forces k, 1 never splits, 0 (automatic) splits only
+// chunks evaluated after their wave's walk has ended (split while the walk
+// runs, a chunk's warps slow the walker down), up to about 32 segment warps
+// an SM (the residency of the segmented kernel) and at most 16 segments a
+// tree.  0 or 1: no split.  The memory the chunk may use bounds it further.
+inline int seg_limit(int ttf_segments, int64_t b, bool walk_over, int64_t num_sms) {
+    if (ttf_segments >= 2) return ttf_segments;
+    if (ttf_segments == 1 || !walk_over || b <= 0) return 0;
+    const int64_t resident = num_sms > 0 ? 32 * num_sms : 32;
+    const int64_t k = resident / b;
+    return (int)(k < 16 ? k : 16);
+}
+
 }  // namespace kc_host

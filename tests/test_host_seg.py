@@ -4,7 +4,8 @@ compiler and checked on random, disjoint regions at random alignments: every
 Fenwick array (n int64, entries 1 .. n, 8-byte aligned) and every stack
 (stack_cap int4, 16-byte aligned) lies inside one region, no two slots
 overlap, a successful carve returns exactly the slots asked for, and
-fit_segments returns the largest k <= kmax that carves (0 below two)."""
+fit_segments returns the largest k <= kmax that carves (0 below two); and the
+segment-count policy of ttf_segments."""
 import ctypes
 import os
 import random
@@ -31,6 +32,9 @@ extern "C" int hs_carve(const uint64_t *p, const uint64_t *bytes, int nr, uint64
     for (size_t i = 0; i < s.size() && i < need; ++i) stks[i] = s[i];
     return ok ? 1 : 0;
 }
+extern "C" int hs_limit(int cfgk, int64_t b, int walk_over, int64_t sms) {
+    return kc_host::seg_limit(cfgk, b, walk_over != 0, sms);
+}
 extern "C" int hs_fit(const uint64_t *p, const uint64_t *bytes, int nr, int64_t b, int kmax,
                       uint64_t bit_bytes, uint64_t stk_bytes) {
     std::vector<uintptr_t> x, y;
@@ -53,6 +57,8 @@ def lib(tmp_path_factory):
     L.hs_carve.restype = ctypes.c_int
     L.hs_carve.argtypes = [u64p, u64p, ctypes.c_int, ctypes.c_uint64, ctypes.c_uint64,
                            ctypes.c_uint64, u64p, u64p]
+    L.hs_limit.restype = ctypes.c_int
+    L.hs_limit.argtypes = [ctypes.c_int, ctypes.c_int64, ctypes.c_int, ctypes.c_int64]
     L.hs_fit.restype = ctypes.c_int
     L.hs_fit.argtypes = [u64p, u64p, ctypes.c_int, ctypes.c_int64, ctypes.c_int,
                          ctypes.c_uint64, ctypes.c_uint64]
@@ -137,3 +143,24 @@ def test_exact_fit_and_shortfall(lib):
     assert lib.hs_carve(_arr([base]), _arr([size - 1]), 1, 2, 8 * n, 16 * cap, bits, stks) == 0
     assert lib.hs_fit(_arr([base]), _arr([size]), 1, 1, 16, 8 * n, 16 * cap) == 2
     assert lib.hs_fit(_arr([base]), _arr([size]), 1, 2, 16, 8 * n, 16 * cap) == 0
+
+
+def test_segment_limit_policy(lib):
+    """ttf_segments = k >= 2 forces k whatever the chunk; 1 never splits; 0
+    splits only after the walk, to about 32 segment warps an SM and at most
+    16 segments a tree."""
+    sms = 152
+    for k in (2, 5, 64):
+        for b in (1, 1000, 100000):
+            for over in (0, 1):
+                assert lib.hs_limit(k, b, over, sms) == k
+    for b in (1, 300, 5000):
+        assert lib.hs_limit(1, b, 1, sms) == 0
+        assert lib.hs_limit(0, b, 0, sms) == 0            # walk still running
+    assert lib.hs_limit(0, 1, 1, sms) == 16               # capped at 16
+    assert lib.hs_limit(0, 2400, 1, sms) == 2             # 4864 resident warps
+    assert lib.hs_limit(0, 1000, 1, sms) == 4
+    assert lib.hs_limit(0, 4864, 1, sms) == 1             # one a tree: no split below 2
+    assert lib.hs_limit(0, 5000, 1, sms) == 0
+    assert lib.hs_limit(0, 0, 1, sms) == 0
+    assert lib.hs_limit(0, 3, 1, 0) == 10                 # unknown SM count: one SM's worth
